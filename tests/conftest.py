@@ -1,0 +1,26 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: long-running")
+
+
+def pytest_collection_modifyitems(config, items):
+    # keep file order (alphabetical) so that the no-allocation test file runs last
+    pass
+
+
+@pytest.fixture(scope="session")
+def lib():
+    """The compiled CUDA library (built on demand)."""
+    import paper_1512_03210_gb300 as fse
+    fse.load()
+    return fse
