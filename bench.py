@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput of the TS2-GauSum split step on GB300 (one JSON line on rank 0).
+
+A bench "step" is one TS2-GauSum split step (Section 4.2, Eqs. tssp1-tssp3)
+of the 3D dipolar workload: 256^3 grid on [-12,12]^3 (512^3 padded density
+spectrum), s=0.6, Omega=0.9, beta=500, lambda=100, tilted dipole axis,
+dt=2.5e-4, synthetic 16-vortex Thomas-Fermi-like initial state. The timed
+region is one fse_step call advancing K steps (kinetic half steps of
+consecutive steps merged, as a user's long run does); psi (134 MB) and the
+padded spectrum (279 MB) exceed the 129 MB L2, so no flush is needed.
+
+Also reported: the float64 GPU path on the same workload, per-kernel event
+timing of the dominant kernel against the measured HBM copy bandwidth, an
+end-to-end figure through fse_step_host (host buffers, copies inside the
+timed region), and the FP64 oracle timed on a bounded sample on host cores.
+
+--impl reference times that oracle alone (rank 0) on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "split steps/s, 256³ dipolar FSE: FP32 vs FP64 path, same accuracy; % HBM roofline"
+UNIT = "split steps/s"
+WORKLOAD = "3d_dipolar_256"
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+# ---------------------------------------------------------------------------
+# CPU side: the FP64 oracle on a bounded sample (spawned before any GPU call)
+# ---------------------------------------------------------------------------
+
+def _oracle_sample(nsteps: int, q) -> None:
+    try:
+        import numpy as np  # noqa: F401
+        import fse_inputs as I
+        import oracle as O
+        d = I.workload(WORKLOAD)
+        p = O.params(d)
+        psi = I.psi0(WORKLOAD)
+        t0 = time.perf_counter()
+        C = O.gausum_multiplier(p)
+        t_pre = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for n in range(nsteps):
+            psi = O.split_step(psi, p, n * p.dt, None, C)
+        dt = time.perf_counter() - t0
+        q.put({"ok": True, "seconds": dt, "steps": nsteps, "precompute_s": t_pre})
+    except Exception as e:  # noqa: BLE001 - reported in the JSON line
+        q.put({"ok": False, "error": repr(e)})
+
+
+def start_oracle(nsteps: int):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    proc = ctx.Process(target=_oracle_sample, args=(nsteps, q), daemon=True)
+    proc.start()
+    return proc, q
+
+
+def finish_oracle(proc, q, timeout=900.0):
+    try:
+        r = q.get(timeout=timeout)
+    except Exception as e:  # noqa: BLE001
+        r = {"ok": False, "error": f"oracle sample did not finish: {e!r}"}
+    proc.join(timeout=5)
+    return r
+
+
+def oracle_baseline_dict(r: dict) -> dict:
+    if not r.get("ok"):
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": r.get("error")}
+    return {"value": r["steps"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{r['steps']} split step(s) of the {WORKLOAD} workload in the FP64 numpy oracle "
+                      f"(single-threaded numpy FFT; kernel transform precomputed outside the timed "
+                      f"region in {r['precompute_s']:.1f} s)"}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("gpu_uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.samples = []
+        self._stop = threading.Event()
+        self._thr = None
+
+    def _once(self):
+        try:
+            out = subprocess.run(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits"],
+                                 capture_output=True, text=True, timeout=5).stdout
+        except Exception:  # noqa: BLE001
+            return
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            if self.uuid and self.uuid not in f[0]:
+                continue
+            self.samples.append(f)
+            break
+
+    def _run(self):
+        while not self._stop.is_set():
+            self._once()
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._once()
+        self._thr = threading.Thread(target=self._run, daemon=True)
+        self._thr.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._thr.join(timeout=10)
+        self._once()
+
+    def summary(self):
+        if not self.samples:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = sorted(v for v in (num(s[1]) for s in self.samples) if v is not None)
+        mx = max((v for v in (num(s[2]) for s in self.samples) if v is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[4 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch of each pass kind (minimum-pass model)
+# ---------------------------------------------------------------------------
+
+def pass_bytes(d: dict) -> dict:
+    c = 8 if d.get("prec", "f32") == "f32" else 16
+    r = c // 2
+    if d["dim"] == 3:
+        nx, ny, nz = d["n"]
+        npsi = nx * ny * nz
+        nhalf = nz * ny * (nx + 1)
+        nspec = nz * 2 * ny * (nx + 1)
+        nchat = (nx + 1) * (ny + 1) * (nz + 1)
+        return {"xfwd": 2 * npsi * c, "xinv": 2 * npsi * c, "E": (2 * npsi + nhalf) * c,
+                "A": (2 * npsi + nhalf) * c, "col": 2 * npsi * c, "kin": 2 * npsi * c,
+                "pad": (nhalf + nspec) * c, "khat": 2 * nspec * c + nchat * r}
+    nx, ny = d["n"]
+    npsi = nx * ny
+    nhalf = ny * (nx + 1)
+    return {"xfwd": 2 * npsi * c, "xinv": 2 * npsi * c, "E": (2 * npsi + nhalf) * c,
+            "A": (2 * npsi + nhalf) * c, "kin": 2 * npsi * c,
+            "khat": 2 * nhalf * c + (nx + 1) * (ny + 1) * r}
+
+
+def step_model_bytes(d: dict) -> int:
+    b = pass_bytes(d)
+    if d["dim"] == 3:
+        return b["A"] + 2 * b["col"] + b["kin"] + b["E"] + 2 * b["pad"] + b["khat"]
+    return b["A"] + b["kin"] + b["E"] + b["khat"]
+
+
+def source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1512_03210_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    try:
+        mp_ = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(mp_["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return 6800.0, "fallback"
+
+
+def traffic_for(kind: str, workload: str):
+    try:
+        t = json.load(open(TRAFFIC_FILE))
+    except Exception:  # noqa: BLE001
+        return None
+    e = t.get(workload, {}).get(kind)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return 0
+    nst = max(1, min(args.steps, 2))
+    proc, q = start_oracle(nst)
+    r = finish_oracle(proc, q)
+    cb = oracle_baseline_dict(r)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": r.get("steps"), "warmup": 0,
+            "ms_per_step": (1000.0 * r["seconds"] / r["steps"]) if r.get("ok") else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "grid": [256, 256, 256],
+                                             "padded": [512, 512, 512], "kernel": "ddi3d"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="fse", choices=["fse", "reference"])
+    ap.add_argument("--f64-steps", type=int, default=40)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--oracle-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank)
+
+    # the oracle process is spawned before the first GPU call
+    oracle = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        oracle = start_oracle(args.oracle_steps)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import fse_inputs as I
+    import paper_1512_03210_gb300 as fse
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    d = I.workload(WORKLOAD)
+    psi0 = I.psi0(WORKLOAD)
+    stream = torch.cuda.current_stream(dev)
+    plan = fse.Plan(d, stream=stream, device=dev)
+    x = plan.to_device(psi0)
+    t = 0.0
+    plan.step(x, t, args.warmup)
+    t += args.warmup * d["dt"]
+    torch.cuda.synchronize(dev)
+
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:  # noqa: BLE001
+        pass
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    l0 = plan.launches
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(uuid) as clk:
+        ev0.record(stream)
+        plan.step(x, t, args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    launches = plan.launches - l0
+    t += args.steps * d["dt"]
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * args.steps / (ms / 1000.0)
+
+    # per-kernel event timing over a second region of the same length
+    fse.fse_plan_profile(plan.handle, True)
+    plan.step(x, t, args.steps)
+    torch.cuda.synchronize(dev)
+    prof = fse.fse_plan_profile_read(plan.handle)
+    fse.fse_plan_profile(plan.handle, False)
+    t += args.steps * d["dt"]
+    tot = sum(v[0] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][0])
+    pb = pass_bytes(d)
+    peak, peak_kind = measured_peak()
+    avg_ms = prof[dom][0] / max(1, prof[dom][1])
+    achieved = pb[dom] / (avg_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"of {peak_kind} (copy bandwidth)",
+                "traffic": traffic_for(dom, WORKLOAD), "algorithmic_bytes": pb[dom],
+                "avg_launch_ms": avg_ms,
+                "share": prof[dom][0] / tot if tot > 0 else None}
+    step_bytes = step_model_bytes(d)
+    kernels = {k: {"ms": v[0], "launches": v[1], "share": v[0] / tot if tot else 0.0,
+                   "gbs": (pb[k] * v[1] / (v[0] / 1000.0) / 1e9) if (v[1] and k in pb and v[0] > 0) else None}
+               for k, v in prof.items() if v[1]}
+
+    # float64 GPU path on the same workload (same scheme, same accuracy class)
+    f64 = None
+    if args.f64_steps > 0:
+        d64 = dict(d, prec="f64")
+        plan64 = fse.Plan(d64, stream=stream, device=dev)
+        x64 = plan64.to_device(psi0)
+        plan64.step(x64, 0.0, 3)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan64.step(x64, 3 * d["dt"], args.f64_steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        v64 = args.f64_steps / (e0.elapsed_time(e1) / 1000.0)
+        f64 = {"value": v64, "unit": UNIT, "steps": args.f64_steps, "speedup_f32_over_f64": value / world / v64}
+        del plan64, x64
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    host = torch.from_numpy(np.ascontiguousarray(psi0.astype(np.complex64))).pin_memory().numpy()
+    plan.step_host(host, 0.0, 1)
+    t0 = time.perf_counter()
+    for i in range(args.e2e_steps):
+        plan.step_host(host, i * d["dt"], 1)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * args.e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(host.nbytes),
+           "calls": args.e2e_steps, "note": "one fse_step_host call (1 split step) per step"}
+
+    if rank != 0:
+        return 0
+    cb = None
+    if oracle is not None:
+        cb = oracle_baseline_dict(finish_oracle(*oracle))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [256, 256, 256], "padded": [512, 512, 512],
+                   "kernel": "ddi3d", "s": d["s"], "omega": d["omega"], "dt": d["dt"],
+                   "l2": "inputs larger than L2 (psi 134 MB, padded spectrum 279 MB); no flush",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "grid_point_steps_per_s": value * 256 ** 3,
+        "model_bytes_per_step": step_bytes,
+        "step_roofline_frac": step_bytes * value / world / 1e9 / peak,
+        "roofline": roofline, "kernels": kernels, "f64": f64, "e2e": e2e,
+        "cpu_baseline": cb, "gpu_launches": launches, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,194 @@
+/*
+ * fse.h -- C ABI of the GB300 TS2-GauSum split-step library.
+ *
+ * The library advances the space-fractional nonlinear Schroedinger /
+ * Gross-Pitaevskii equation with rotation and nonlocal (Coulomb or dipolar)
+ * interaction (Antoine, Tang & Zhang, arXiv 1512.03210, Eqs. SFSE and
+ * NonLocalPot) by the second-order time-splitting Fourier pseudo-spectral
+ * scheme TS2-GauSum (Section 4.2, Eqs. tssp1-tssp3), written in the rotating
+ * Lagrangian coordinates x~ = A(t)^T x (Eqs. Amatrix, transform, FSE1_Rot),
+ * with the nonlocal term evaluated by the Gaussian-sum method (Section 2,
+ * Eqs. key_form00, GS-Gene, FourSeriB3, tensor, taylor).
+ *
+ * Conventions shared by every call
+ * - The unknown is phi(x~, t) = psi(A(t) x~, t) on the box B = prod [lo_j, hi_j)
+ *   (Eq. transform79), sampled at x~_l = lo + l h, l = 0..n-1, h = (hi-lo)/n.
+ * - Layout: row-major [nz][ny][nx] (3D) or [ny][nx] (2D), x fastest,
+ *   interleaved complex: float2 for FSE_F32 plans, double2 for FSE_F64 plans.
+ * - Device pointers are CUDA device memory on the plan's device; the caller
+ *   owns every buffer (wave function, cotangent, workspace). The library
+ *   allocates no device memory: all scratch lives in the caller's workspace.
+ * - Calls are asynchronous on the plan's stream unless stated otherwise; a
+ *   CUDA launch or copy error is reported as FSE_ERR_CUDA by the call that
+ *   observes it. No call throws across the ABI.
+ * - Supported grid sizes per axis: n in {8,12,16,24,32,48,64,96,128,192,256,
+ *   384,512}; padded lengths 2n are handled internally.
+ * - A plan is not thread-safe: one host thread at a time per plan.
+ */
+#ifndef FSE_H_
+#define FSE_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fse_plan* fse_plan_t;
+
+typedef enum {
+  FSE_OK = 0,
+  FSE_ERR_INVALID = 1,      /* a null pointer, a bad parameter or call order */
+  FSE_ERR_UNSUPPORTED = 2,  /* a valid request this build does not implement */
+  FSE_ERR_NOMEM = 3,        /* the workspace given is smaller than required */
+  FSE_ERR_CUDA = 4,         /* a CUDA runtime call failed (message in fse_plan_error) */
+  FSE_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+  FSE_ERR_NONFINITE = 6     /* a reduction met NaN or Inf */
+} fse_status;
+
+typedef enum { FSE_KERNEL_NONE = 0, FSE_KERNEL_COULOMB = 1, FSE_KERNEL_DDI3D = 2 } fse_kernel;
+typedef enum { FSE_F32 = 0, FSE_F64 = 1 } fse_prec;
+
+/*
+ * Problem parameters (Eq. SFSE; Eq. Kernel; Eq. harm_poten; Section 4.2).
+ *   dim        2 or 3
+ *   n[j], lo[j], hi[j]   grid of axis j (x, y, z); n[2] ignored for dim 2
+ *   s, m       fractional order s > 0 and mass m >= 0 of (-Lap + m^2)^s / 2
+ *   omega      rotation speed Omega of the -Omega L_z term (Eq. Amatrix)
+ *   beta       local cubic interaction strength
+ *   lambda     nonlocal interaction strength
+ *   dt         time step (may be negative: the scheme is time-reversible)
+ *   kernel     fse_kernel: none, Coulomb-type 1/(2^{d-1} pi |x|^mu), or 3D DDI
+ *   mu         Coulomb exponent; this build supports mu = 1
+ *   dip_n[3]   dipole axis n (unit vector) for FSE_KERNEL_DDI3D
+ *   gamma[3]   harmonic trap frequencies (Eq. harm_poten)
+ *   gs_delta, gs_h, gs_tmin  Gaussian-sum fit (Eq. GS-Gene): near-field
+ *              radius in unit-box units, sinc-quadrature step and lower
+ *              end; 0 selects 1e-3, 0.125, -36
+ *   prec       fse_prec: arithmetic of the split step
+ *   renormalize  0: the paper's scheme; 1: after each step rescale psi so that
+ *              its float64 mass equals the mass at the start of the fse_step
+ *              call (holds the float32 mass drift; not part of the paper)
+ */
+typedef struct {
+  int dim;
+  int n[3];
+  double lo[3], hi[3];
+  double s, m, omega, beta, lambda, dt;
+  int kernel;
+  double mu;
+  double dip_n[3];
+  double gamma[3];
+  double gs_delta, gs_h, gs_tmin;
+  int prec;
+  int renormalize;
+} fse_params;
+
+/* Observables (Eqs. mass, energy, AME, CoM, ConWidth) at time t, in float64.
+ * energy = e_kin + e_pot + e_int + e_non + e_rot with e_rot = -Omega <L_z>;
+ * xc and width are in the frame of Eq. SFSE (x = A(t) x~); unused z entries 0. */
+typedef struct {
+  double mass, e_kin, e_pot, e_int, e_non, e_rot, energy, lz;
+  double xc[3], width[3];
+} fse_obs;
+
+/* Validate *params, create a plan bound to cuda_stream (a cudaStream_t; NULL
+ * = legacy default stream) on the current CUDA device, and return in
+ * *workspace_bytes the size of the device workspace the caller must supply.
+ * Errors: FSE_ERR_INVALID (null pointers, dim, s <= 0, box, dt = 0, kernel
+ * and dim mismatch), FSE_ERR_UNSUPPORTED (a size outside the supported set,
+ * mu != 1). On error *out is NULL. */
+fse_status fse_plan_create(const fse_params* params, void* cuda_stream, fse_plan_t* out,
+                           size_t* workspace_bytes);
+
+/* Attach caller-owned device memory of at least workspace_bytes bytes
+ * (256-byte aligned) to the plan; the plan keeps the pointer, not ownership.
+ * Errors: FSE_ERR_INVALID (null, misaligned), FSE_ERR_NOMEM (too small). */
+fse_status fse_plan_set_workspace(fse_plan_t plan, void* dev_ptr, size_t bytes);
+
+/* Once per plan, after set_workspace: build in the workspace the twiddle
+ * tables, the Gaussian-sum tables g_q(k_j) (Eq. tensor) and the kernel
+ * transform C^(k) = sum_q w_q prod_j g_q(k_j) + I0 - I2 |k|^2/(2d) on the
+ * non-negative padded frequencies (Section 2, Eqs. GS-Gene, tensor, taylor),
+ * in float64, stored in the plan's precision. Asynchronous. */
+fse_status fse_kernel_precompute(fse_plan_t plan);
+
+/* Advance psi (device, plan layout, in place) by nsteps TS2-GauSum steps
+ * from t0 (Eqs. tssp1-tssp3; adjacent kinetic half steps of consecutive
+ * steps are merged). gamma_per_step (host, nullable) holds [nsteps][dim]
+ * trap frequencies, constant over each step (the parameters' gamma when
+ * NULL). Asynchronous. Errors: FSE_ERR_INVALID (null plan/psi, nsteps < 0,
+ * precompute not run). */
+fse_status fse_step(fse_plan_t plan, void* psi, double t0, int nsteps,
+                    const double* gamma_per_step);
+
+/* As fse_step with psi in HOST memory (pinned or pageable): copies psi into
+ * the workspace's staging slot, steps, copies it back and synchronises the
+ * plan's stream before returning. */
+fse_status fse_step_host(fse_plan_t plan, void* psi_host, double t0, int nsteps,
+                         const double* gamma_per_step);
+
+/* Pull a cotangent back through the single step t_n -> t_n + dt taken from
+ * psi_n (device, unchanged). g (device, plan layout) holds on entry the
+ * cotangent dJ/dRe psi_{n+1} + i dJ/dIm psi_{n+1} and on return the cotangent
+ * at psi_n. gamma_n (host, nullable, [dim]) are the step's trap frequencies;
+ * dgamma_n (host, nullable, [dim]) receives dJ/dgamma_n (the call then
+ * synchronises the stream). The paper has no adjoint: this is the transpose
+ * of the real-linearised map of Eqs. tssp1-tssp3. Errors: FSE_ERR_INVALID
+ * (null or misaligned buffers, precompute not run), FSE_ERR_UNSUPPORTED
+ * (a plan with renormalize = 1). Uses the workspace's scratch wave function
+ * and spectrum, so it must not overlap other calls on the same plan. */
+fse_status fse_step_adjoint(fse_plan_t plan, const void* psi_n, void* g, double t_n,
+                            const double* gamma_n, double* dgamma_n);
+
+/* Observables of psi (device, unchanged) at time t with trap frequencies
+ * gamma (host, nullable, [dim]); float64 reductions on the device, one
+ * device-to-host copy; synchronises the plan's stream. */
+fse_status fse_observables(fse_plan_t plan, const void* psi, double t, const double* gamma,
+                           fse_obs* out);
+
+/* Rebind the plan to another stream (a cudaStream_t on the same device). */
+fse_status fse_plan_set_stream(fse_plan_t plan, void* cuda_stream);
+
+/* Release the plan's host memory (never the caller's workspace). NULL is a no-op. */
+fse_status fse_plan_destroy(fse_plan_t plan);
+
+/* Static description of a status code. */
+const char* fse_status_string(fse_status status);
+
+/* Detail of the last error recorded on this plan ("" if none). */
+const char* fse_plan_error(fse_plan_t plan);
+
+/* Number of kernel launches the plan has issued since creation. */
+long long fse_plan_launch_count(fse_plan_t plan);
+
+/* Pass kinds for per-kernel timing (see fse_plan_profile). */
+typedef enum {
+  FSE_PASS_XFWD = 0,    /* forward FFT along x (start of a call) */
+  FSE_PASS_XINV = 1,    /* inverse FFT along x (end of a call, or no nonlocal term) */
+  FSE_PASS_E = 2,       /* inverse x, density, zero-padded real-to-complex x transform */
+  FSE_PASS_A = 3,       /* complex-to-real x transform, potential phase, forward x */
+  FSE_PASS_COL = 4,     /* plain transform along y of the wave function */
+  FSE_PASS_KIN = 5,     /* forward, kinetic phase, inverse along the last axis */
+  FSE_PASS_PAD = 6,     /* zero-padded forward / cropped inverse along y of the density */
+  FSE_PASS_KHAT = 7,    /* forward, kernel transform, inverse along the last padded axis */
+  FSE_PASS_PRE = 8,     /* once-per-plan tables */
+  FSE_PASS_OTHER = 9,   /* observables and adjoint kernels */
+  FSE_NPASS = 10
+} fse_pass_kind;
+
+/* Per-kernel timing (tracing). With enable != 0 every later launch of the
+ * plan is bracketed by two CUDA events on the plan's stream; enable = 0 stops
+ * recording. Adds a few microseconds of host time per launch. */
+fse_status fse_plan_profile(fse_plan_t plan, int enable);
+
+/* Synchronise on the recorded events and return, per fse_pass_kind, the
+ * summed device time in milliseconds (ms[FSE_NPASS]) and the number of
+ * launches (count[FSE_NPASS]) since the last read; then clear the record. */
+fse_status fse_plan_profile_read(fse_plan_t plan, double* ms, long long* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FSE_H_ */

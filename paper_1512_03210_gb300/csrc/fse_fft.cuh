@@ -1,0 +1,231 @@
+// fse_fft.cuh -- shared-memory Stockham FFT used by every pass of the split step.
+//
+// The transform along one grid axis is done on a tile of NCOL independent
+// lines held in shared memory as buf[j * LDS + c] (j = position along the
+// line, c = line within the tile, LDS = NCOL + 1). Each radix-R pass of the
+// mixed-radix Stockham autosort algorithm (radices 8, 4, 3, 2) reads R
+// elements at stride N/R, applies the twiddles, does an in-register DFT of
+// size R and writes the R results at stride Ns; all reads of a pass happen
+// before a barrier and all writes after it, so one buffer suffices.
+//
+// The forward transform is unnormalised, X_k = sum_j x_j exp(-2 pi i jk/N);
+// the inverse uses the conjugate twiddles and is also unnormalised (the
+// scale 1/N is applied by the pass that owns the spectral multiplier).
+// Twiddles come from a table tw[m] = exp(-2 pi i m/N) built in float64 and
+// rounded to the plan's precision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fse {
+
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { typedef float2 T; };
+template <> struct Cplx<double> { typedef double2 T; };
+
+__device__ __forceinline__ float2 mk(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk(double a, double b) { return make_double2(a, b); }
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return mk(a.x + b.x, a.y + b.y); }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return mk(a.x - b.x, a.y - b.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return mk(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+// multiply by -i (DIR < 0) or +i (DIR > 0)
+template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
+  return DIR < 0 ? mk(a.y, -a.x) : mk(-a.y, a.x);
+}
+
+// ---------------------------------------------------------------------------
+// Radix plans: N = 2^a 3^b (b <= 1) split into passes of radix 3, 8, 4, 2.
+// ---------------------------------------------------------------------------
+struct RadixPlan {
+  int npass;
+  int r[8];
+};
+
+__host__ __device__ constexpr RadixPlan radix_plan(int N) {
+  RadixPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}};
+  int m = N, a = 0;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  if (m == 3) p.r[p.npass++] = 3;
+  int q = a / 3, rem = a % 3;
+  if (rem == 0) {
+    for (int i = 0; i < q; ++i) p.r[p.npass++] = 8;
+  } else if (rem == 1) {
+    if (q >= 1) {
+      for (int i = 0; i < q - 1; ++i) p.r[p.npass++] = 8;
+      p.r[p.npass++] = 4;
+      p.r[p.npass++] = 4;
+    } else {
+      p.r[p.npass++] = 2;
+    }
+  } else {
+    for (int i = 0; i < q; ++i) p.r[p.npass++] = 8;
+    p.r[p.npass++] = 4;
+  }
+  return p;
+}
+
+__host__ __device__ constexpr bool fft_size_ok(int N) {
+  int m = N;
+  while (m % 2 == 0) m /= 2;
+  return N >= 4 && (m == 1 || m == 3);
+}
+
+// ---------------------------------------------------------------------------
+// In-register DFTs of size R. DIR = -1 forward, +1 inverse.
+// ---------------------------------------------------------------------------
+template <int DIR, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+  C t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <int DIR, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  C s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  C s13 = cadd(a1, a3), d13 = mul_i<DIR>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+// Irrational butterfly constants as a head + tail pair, so that a product
+// x * c is rounded once from its exact value (fma(x, head, x * tail)). With a
+// single rounded float constant every radix-8 (or radix-3) pass would scale
+// half of its outputs by the same |1 + eps| and the norm of the field would
+// drift by ~1e-8 per pass, always in the same direction.
+template <typename R> struct Kc;
+template <> struct Kc<float> {
+  static constexpr double kH = 0.70710678118654752440084436210484904;  // sqrt(1/2)
+  static constexpr double kS = 0.86602540378443864676372317075293618;  // sqrt(3)/2
+  static constexpr float h1 = (float)kH;
+  static constexpr float h2 = (float)(kH - (double)(float)kH);
+  static constexpr float s1 = (float)kS;
+  static constexpr float s2 = (float)(kS - (double)(float)kS);
+};
+template <> struct Kc<double> {
+  static constexpr double h1 = 0.70710678118654752440084436210484904, h2 = 0.0;
+  static constexpr double s1 = 0.86602540378443864676372317075293618, s2 = 0.0;
+};
+__device__ __forceinline__ float mulk(float x, float k1, float k2) { return fmaf(x, k1, x * k2); }
+__device__ __forceinline__ double mulk(double x, double k1, double) { return x * k1; }
+
+template <int DIR, typename C> __device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
+  typedef decltype(a0.x) R;
+  const R c = R(-0.5);
+  C t = cadd(a1, a2);
+  C d = csub(a1, a2);
+  C m = mk(a0.x + c * t.x, a0.y + c * t.y);
+  // i * DIR * sin(2 pi/3) * (a1 - a2): exp(DIR 2 pi i/3) = c + i DIR sin(2 pi/3)
+  const R sy = mulk(d.y, Kc<R>::s1, Kc<R>::s2), sx = mulk(d.x, Kc<R>::s1, Kc<R>::s2);
+  C e = DIR < 0 ? mk(sy, -sx) : mk(-sy, sx);
+  a0 = cadd(a0, t);
+  a1 = cadd(m, e);
+  a2 = csub(m, e);
+}
+
+template <int DIR, typename C> __device__ __forceinline__ void dft8(C* v) {
+  typedef decltype(v[0].x) R;
+  // even / odd halves
+  dft4<DIR>(v[0], v[2], v[4], v[6]);
+  dft4<DIR>(v[1], v[3], v[5], v[7]);
+  // twiddle odd half by w8^k, w8 = exp(DIR i pi/4):
+  // w8^1 = h (1 + DIR i); w8^2 = DIR i; w8^3 = h (-1 + DIR i), h = sqrt(1/2)
+  C o1 = v[3], o2 = v[5], o3 = v[7];
+  const R a1 = o1.x - R(DIR) * o1.y, b1 = o1.y + R(DIR) * o1.x;
+  const R a3 = -o3.x - R(DIR) * o3.y, b3 = -o3.y + R(DIR) * o3.x;
+  C t1 = mk(mulk(a1, Kc<R>::h1, Kc<R>::h2), mulk(b1, Kc<R>::h1, Kc<R>::h2));
+  C t2 = mul_i<DIR>(o2);
+  C t3 = mk(mulk(a3, Kc<R>::h1, Kc<R>::h2), mulk(b3, Kc<R>::h1, Kc<R>::h2));
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, t1);
+  v[5] = csub(e1, t1);
+  v[2] = cadd(e2, t2);
+  v[6] = csub(e2, t2);
+  v[3] = cadd(e3, t3);
+  v[7] = csub(e3, t3);
+}
+
+template <int R, int DIR, typename C> __device__ __forceinline__ void dft(C* v) {
+  if constexpr (R == 2) {
+    dft2<DIR>(v[0], v[1]);
+  } else if constexpr (R == 3) {
+    dft3<DIR>(v[0], v[1], v[2]);
+  } else if constexpr (R == 4) {
+    dft4<DIR>(v[0], v[1], v[2], v[3]);
+  } else {
+    static_assert(R == 8, "radix");
+    dft8<DIR>(v);
+  }
+}
+
+// One Stockham pass of radix R over NCOL lines of length N in shared memory.
+template <typename C, int N, int NCOL, int NT, int DIR, int R, int NS>
+__device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) {
+  constexpr int LDS = NCOL + 1;
+  constexpr int ITEMS = NCOL * (N / R);
+  constexpr int PER = (ITEMS + NT - 1) / NT;
+  const int tid = threadIdx.x;
+  C v[PER][R];
+#pragma unroll
+  for (int it = 0; it < PER; ++it) {
+    const int w = tid + it * NT;
+    if ((ITEMS % NT) == 0 || w < ITEMS) {
+      const int c = w % NCOL, j = w / NCOL;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[it][r] = buf[(j + r * (N / R)) * LDS + c];
+      if constexpr (NS > 1) {
+        const int k = j % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C w8 = __ldg(&tw[(k * r) * (N / (NS * R))]);
+          v[it][r] = DIR < 0 ? cmul(v[it][r], w8) : cmulc(v[it][r], w8);
+        }
+      }
+      dft<R, DIR>(v[it]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < PER; ++it) {
+    const int w = tid + it * NT;
+    if ((ITEMS % NT) == 0 || w < ITEMS) {
+      const int c = w % NCOL, j = w / NCOL;
+      const int k = j % NS;
+      const int base = (j / NS) * NS * R + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[(base + r * NS) * LDS + c] = v[it][r];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename C, int N, int NCOL, int NT, int DIR, int PASS, int NS>
+__device__ __forceinline__ void stockham_rec(C* buf, const C* __restrict__ tw) {
+  constexpr RadixPlan P = radix_plan(N);
+  if constexpr (PASS < P.npass) {
+    constexpr int R = P.r[PASS];
+    stockham_pass<C, N, NCOL, NT, DIR, R, NS>(buf, tw);
+    stockham_rec<C, N, NCOL, NT, DIR, PASS + 1, NS * R>(buf, tw);
+  }
+}
+
+// Full transform of NCOL lines of length N held in buf (caller synchronised
+// before the call; the call ends with a barrier).
+template <typename C, int N, int NCOL, int NT, int DIR>
+__device__ __forceinline__ void fft_tile(C* buf, const C* __restrict__ tw) {
+  static_assert(fft_size_ok(N), "FFT length must be 2^a or 3*2^a");
+  stockham_rec<C, N, NCOL, NT, DIR, 0, 1>(buf, tw);
+}
+
+}  // namespace fse

@@ -1,0 +1,158 @@
+// fse_precompute.cu -- once-per-plan float64 tables (twiddles, Gaussian-sum kernel transform).
+//
+// Kernel transform of the cube-truncated Coulomb kernel (Section 2):
+//   C^(k) = sum_q w_q prod_j g_q(k_j) + I0 - I2 |k|^2 / (2d)          (Eqs. tensor, taylor)
+//   g_q(k) = int_{-W}^{W} exp(-tau_q^2 y^2) cos(k y) dy               (Eq. tensor)
+// with the zero-padded period 2W per axis (W the box width), k = pi p / W,
+// p = 0..n. Wide Gaussians (tau W < 6) are integrated by composite
+// Gauss-Legendre quadrature on [0, W]; for narrow ones the truncation at W
+// changes the integral by less than erfc(6) ~ 2e-17 relative, so the
+// full-line value sqrt(pi)/tau exp(-k^2/(4 tau^2)) is used.
+#include <cuda_runtime.h>
+
+#include "fse_fft.cuh"
+
+namespace fse {
+
+// tw[m] = exp(-2 pi i m / L), m = 0..L-1, from float64 sincospi. For float
+// tables the pair (c, s) is chosen among the float neighbours of the float64
+// values as the one with |c + i s| closest to 1: every element of a transform
+// meets the same table entries in every step, so a magnitude error of an
+// entry would otherwise act as a fixed gain and make the norm drift.
+__device__ __forceinline__ void round_pair(double c, double s, float2* out) {
+  const float c0 = (float)c, s0 = (float)s;
+  const float cc[2] = {c0, (double)c0 > c ? nextafterf(c0, -2.f) : nextafterf(c0, 2.f)};
+  const float ss[2] = {s0, (double)s0 > s ? nextafterf(s0, -2.f) : nextafterf(s0, 2.f)};
+  double best = 1e300;
+  float2 r = make_float2(c0, s0);
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      const double n = (double)cc[i] * cc[i] + (double)ss[j] * ss[j] - 1.0;
+      if (fabs(n) < best) {
+        best = fabs(n);
+        r = make_float2(cc[i], ss[j]);
+      }
+    }
+  *out = r;
+}
+__device__ __forceinline__ void round_pair(double c, double s, double2* out) { *out = make_double2(c, s); }
+
+template <typename Real>
+__global__ void k_twiddles(typename Cplx<Real>::T* tw, int L) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= L) return;
+  double s, c;
+  sincospi(-2.0 * (double)m / (double)L, &s, &c);
+  round_pair(c, s, &tw[m]);
+}
+
+// Quadrature nodes on [0, W]: npan panels of ngl Gauss-Legendre points.
+// cs[y * (n+1) + p] = cos(k_p y_y); e[qw * ny + y] = w_y exp(-tau_q^2 y_y^2) for the wide q.
+__global__ void k_gs_cos(double* cs, const double* glx, const double* glw, int ngl, int npan,
+                         double W, int n, double* ynode, double* ywt) {
+  const int ny = ngl * npan;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= ny * (n + 1)) return;
+  const int y = idx / (n + 1), p = idx % (n + 1);
+  const int pan = y / ngl, g = y % ngl;
+  const double hw = 0.5 * W / npan;
+  const double yy = hw * (2 * pan + 1) + hw * glx[g];
+  // k_p y = (pi p / W) y
+  cs[idx] = cospi((double)p * yy / W);
+  if (p == 0) {
+    ynode[y] = yy;
+    ywt[y] = hw * glw[g];
+  }
+}
+
+__global__ void k_gs_table(double* g, const double* cs, const double* ynode, const double* ywt,
+                           const double* tau, int Q, int n, int ny, double W) {
+  const int q = blockIdx.x;
+  const double t = tau[q];
+  extern __shared__ double ew[];
+  const bool wide = t * W < 6.0;
+  if (wide) {
+    for (int y = threadIdx.x; y < ny; y += blockDim.x) ew[y] = ywt[y] * exp(-(t * ynode[y]) * (t * ynode[y]));
+    __syncthreads();
+  }
+  for (int p = threadIdx.x; p <= n; p += blockDim.x) {
+    double v;
+    if (wide) {
+      double acc = 0.0;
+      for (int y = 0; y < ny; ++y) acc = fma(ew[y], cs[(long long)y * (n + 1) + p], acc);
+      v = 2.0 * acc;
+    } else {
+      const double k = 3.14159265358979323846 * (double)p / W;
+      v = 1.7724538509055160273 / t * exp(-k * k / (4.0 * t * t));
+    }
+    g[(long long)q * (n + 1) + p] = v;
+  }
+}
+
+// C^ on the octant [nz+1][ny+1][nx+1] (dim 3) or [ny+1][nx+1] (dim 2).
+template <typename Real>
+__global__ void k_chat(Real* out, const double* w, const double* gx, const double* gy,
+                       const double* gz, int Q, int nx, int ny, int nz, int dim, double dkx,
+                       double dky, double dkz, double I0, double I2) {
+  const int px = blockIdx.x * blockDim.x + threadIdx.x;
+  const int py = blockIdx.y;
+  const int pz = blockIdx.z;
+  extern __shared__ double wyz[];   // w_q g_y[q][py] g_z[q][pz]
+  for (int q = threadIdx.x; q < Q; q += blockDim.x) {
+    double v = w[q] * gy[(long long)q * (ny + 1) + py];
+    if (dim == 3) v *= gz[(long long)q * (nz + 1) + pz];
+    wyz[q] = v;
+  }
+  __syncthreads();
+  if (px > nx) return;
+  double acc = 0.0;
+  for (int q = 0; q < Q; ++q) acc = fma(wyz[q], gx[(long long)q * (nx + 1) + px], acc);
+  const double kx = dkx * px, ky = dky * py, kz = dim == 3 ? dkz * pz : 0.0;
+  acc += I0 - I2 * (kx * kx + ky * ky + kz * kz) / (2.0 * dim);
+  out[((long long)pz * (ny + 1) + py) * (nx + 1) + px] = Real(acc);
+}
+
+template <typename Real>
+cudaError_t launch_twiddles(void* tw, int L, cudaStream_t st) {
+  k_twiddles<Real><<<(L + 127) / 128, 128, 0, st>>>(reinterpret_cast<typename Cplx<Real>::T*>(tw), L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gs_axis(double* g, double* cs, double* ynode, double* ywt, const double* tau,
+                           int Q, const double* glx, const double* glw, int ngl, int npan, double W,
+                           int n, cudaStream_t st) {
+  const int ny = ngl * npan;
+  const int tot = ny * (n + 1);
+  k_gs_cos<<<(tot + 255) / 256, 256, 0, st>>>(cs, glx, glw, ngl, npan, W, n, ynode, ywt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = sizeof(double) * (size_t)ny;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_gs_table, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_gs_table<<<Q, 128, smem, st>>>(g, cs, ynode, ywt, tau, Q, n, ny, W);
+  return cudaGetLastError();
+}
+
+template <typename Real>
+cudaError_t launch_chat(void* out, const double* w, const double* gx, const double* gy,
+                        const double* gz, int Q, int nx, int ny, int nz, int dim, double dkx,
+                        double dky, double dkz, double I0, double I2, cudaStream_t st) {
+  dim3 grid((nx + 1 + 127) / 128, ny + 1, dim == 3 ? nz + 1 : 1);
+  const size_t smem = sizeof(double) * (size_t)Q;
+  k_chat<Real><<<grid, 128, smem, st>>>(reinterpret_cast<Real*>(out), w, gx, gy, gz, Q, nx, ny, nz,
+                                        dim, dkx, dky, dkz, I0, I2);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_twiddles<float>(void*, int, cudaStream_t);
+template cudaError_t launch_twiddles<double>(void*, int, cudaStream_t);
+template cudaError_t launch_chat<float>(void*, const double*, const double*, const double*,
+                                        const double*, int, int, int, int, int, double, double,
+                                        double, double, double, cudaStream_t);
+template cudaError_t launch_chat<double>(void*, const double*, const double*, const double*,
+                                         const double*, int, int, int, int, int, double, double,
+                                         double, double, double, cudaStream_t);
+
+}  // namespace fse

@@ -1,0 +1,79 @@
+"""The C-ABI library loads on a machine without a GPU, exports every function
+declared in include/fse.h, and validates plan parameters on the host."""
+import ctypes as ct
+import os
+
+import pytest
+
+import fse_inputs as I
+import paper_1512_03210_gb300 as fse
+
+
+def test_header_declares_the_boundary():
+    names = fse.header_functions()
+    for required in ("fse_plan_create", "fse_plan_set_workspace", "fse_kernel_precompute", "fse_step",
+                     "fse_step_adjoint", "fse_observables", "fse_plan_destroy", "fse_status_string"):
+        assert required in names
+
+
+def test_library_exports_every_header_function():
+    lib = fse.load()
+    for name in fse.header_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings():
+    assert fse.fse_status_string(0) == "ok"
+    assert "workspace" in fse.fse_status_string(3)
+
+
+def _create(p):
+    lib = fse.load()
+    fp = fse.to_params(p)
+    h = ct.c_void_p()
+    nb = ct.c_size_t()
+    st = lib.fse_plan_create(ct.byref(fp), None, ct.byref(h), ct.byref(nb))
+    if h.value:
+        lib.fse_plan_destroy(h)
+    return st, nb.value
+
+
+def test_plan_validation_on_host():
+    good = I.workload("2d_coulomb_128")
+    st, nb = _create(good)
+    assert st == 0 and nb > 0
+    # workspace grows with the padded spectrum: 3D 256^3 float32 needs S = 256*512*272 c64
+    st, nb3 = _create(I.workload("3d_dipolar_256"))
+    assert st == 0 and nb3 > 256 * 512 * 272 * 8
+    assert _create(dict(good, dim=4))[0] == 1
+    assert _create(dict(good, s=0.0))[0] == 1
+    assert _create(dict(good, dt=0.0))[0] == 1
+    assert _create(dict(good, hi=(-9.0, 8.0)))[0] == 1
+    assert _create(dict(good, kernel="ddi3d"))[0] == 1           # the DDI kernel needs dim 3
+    assert _create(dict(good, n=(100, 128)))[0] == 2             # 100 is not 2^a or 3*2^a
+    assert _create(dict(good, n=(1024, 1024)))[0] == 2           # above the largest size
+    assert _create(dict(good, mu=0.5))[0] == 2
+
+
+def test_null_arguments_rejected():
+    lib = fse.load()
+    assert lib.fse_plan_create(None, None, None, None) == 1
+    assert lib.fse_step(None, None, ct.c_double(0.0), 1, None) == 1
+    assert lib.fse_kernel_precompute(None) == 1
+    assert lib.fse_plan_destroy(None) == 0
+
+
+def test_set_workspace_checks_size_and_alignment():
+    lib = fse.load()
+    fp = fse.to_params(I.workload("2d_coulomb_128"))
+    h = ct.c_void_p()
+    nb = ct.c_size_t()
+    assert lib.fse_plan_create(ct.byref(fp), None, ct.byref(h), ct.byref(nb)) == 0
+    try:
+        # host-side checks only: no device memory is touched
+        assert lib.fse_plan_set_workspace(h, ct.c_void_p(4096 * 1024), nb.value - 1) == 3
+        assert lib.fse_plan_set_workspace(h, ct.c_void_p(4096 * 1024 + 8), nb.value) == 1
+        assert lib.fse_step(h, ct.c_void_p(4096 * 1024), ct.c_double(0.0), 1, None) == 1  # no precompute
+        assert "precompute" in fse.fse_plan_error(h)
+    finally:
+        lib.fse_plan_destroy(h)
