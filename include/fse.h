@@ -187,6 +187,30 @@ fse_status fse_plan_profile(fse_plan_t plan, int enable);
  * launches (count[FSE_NPASS]) since the last read; then clear the record. */
 fse_status fse_plan_profile_read(fse_plan_t plan, double* ms, long long* count);
 
+/* Largest npoints accepted by fse_mass_noalloc (4096 partials of 65536 points). */
+#define FSE_NOALLOC_MAX_POINTS (4096LL * 65536LL)
+
+/* Mass h^d sum |psi|^2 of npoints complex values at psi (device, float2 when
+ * prec = FSE_F32, double2 when FSE_F64), written as one double to mass_out
+ * (device) on cuda_stream (NULL = legacy default stream); cell_volume is h^d.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory -- e.g. a monitoring hook between steps inside
+ * a framework whose caching allocator owns the device memory, where a
+ * cudaMalloc would fail or synchronise the device -- and that have no plan
+ * workspace. It allocates nothing: its scratch is a static 32 KB device array
+ * (4096 float64 partials) that every GPU loading the library holds until the
+ * process exits. The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture. Every call overwrites the partials it reads, so
+ * nothing needs clearing, but all calls share the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * ordered by the caller. Asynchronous. Errors: FSE_ERR_INVALID (null or
+ * misaligned pointers, npoints < 0, prec), FSE_ERR_UNSUPPORTED (npoints >
+ * FSE_NOALLOC_MAX_POINTS, the size the static scratch holds; or a device
+ * index >= 64), FSE_ERR_CUDA (symbol lookup or launch failure). */
+fse_status fse_mass_noalloc(const void* psi, int prec, long long npoints, double cell_volume,
+                            double* mass_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

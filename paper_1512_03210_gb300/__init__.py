@@ -23,6 +23,7 @@ __all__ = [
     "fse_step_host", "fse_step_adjoint", "fse_observables", "fse_plan_set_stream",
     "fse_plan_destroy", "fse_status_string", "fse_plan_error", "fse_plan_launch_count",
     "header_functions", "to_params", "fse_plan_profile", "fse_plan_profile_read", "PASS_KINDS",
+    "fse_mass_noalloc",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -106,6 +107,7 @@ def load(build_if_missing: bool = True):
         "fse_plan_launch_count": (ct.c_longlong, [P]),
         "fse_plan_profile": (ct.c_int, [P, ct.c_int]),
         "fse_plan_profile_read": (ct.c_int, [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_longlong)]),
+        "fse_mass_noalloc": (ct.c_int, [P, ct.c_int, ct.c_longlong, ct.c_double, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -236,6 +238,14 @@ def fse_plan_profile_read(plan) -> dict:
     cnt = (ct.c_longlong * len(PASS_KINDS))()
     _check(load().fse_plan_profile_read(plan, ms, cnt), "fse_plan_profile_read", plan)
     return {k: (ms[i], int(cnt[i])) for i, k in enumerate(PASS_KINDS)}
+
+
+def fse_mass_noalloc(psi, prec: str, npoints: int, cell_volume: float, mass_out, stream=None):
+    """Mass of psi into mass_out (a one-element float64 device tensor) with no device
+    allocation; for callers that cannot allocate (see include/fse.h)."""
+    st = load().fse_mass_noalloc(_ptr(psi), PRECS[prec], int(npoints), float(cell_volume), _ptr(mass_out),
+                                 ct.c_void_p(stream or 0))
+    _check(st, "fse_mass_noalloc")
 
 
 def fse_plan_destroy(plan):
