@@ -19,6 +19,9 @@
 
 namespace fse {
 template <typename Real> cudaError_t launch_twiddles(void* tw, int L, cudaStream_t st);
+template <typename Real>
+cudaError_t launch_kin_table(void* half, void* full, int nx, int ny, int nz, double dkx, double dky, double dkz,
+                             double s, double m2, double dt, cudaStream_t st);
 cudaError_t launch_gs_axis(double* g, double* cs, double* ynode, double* ywt, const double* tau,
                            int Q, const double* glx, const double* glw, int ngl, int npan,
                            double W, int n, cudaStream_t st);
@@ -254,29 +257,26 @@ XArgs x_args(fse_plan* P, void* psi, void* spec) {
 // on a field already transformed along x: fwd-y, fwd-z . phase . inv-z, inv-y
 // (3D) or fwd-y . phase . inv-y (2D). On exit the field is x-spectral.
 fse_status kinetic_yz(fse_plan* P, void* psi, double f, double dt) {
+  (void)dt;  // the phase tables were built with the plan's dt
   MulArgs m;
   std::memset(&m, 0, sizeof(m));
   m.mode = MUL_KIN;
-  m.c0 = f * dt / 4.0;
-  m.s = P->p.s;
-  m.m2 = P->p.m * P->p.m;
-  m.lx = P->nx;
-  m.dkx = 2 * kPi / (P->p.hi[0] - P->p.lo[0]);
+  if (f == 1.0 || f == -1.0) {
+    m.kin = P->ws_ptr(P->off_kin_half);
+  } else if (f == 2.0) {
+    m.kin = P->ws_ptr(P->off_kin_full);
+  } else {
+    return fail(P, FSE_ERR_INVALID, "kinetic factor must be 1, 2 or -1");
+  }
+  m.conj = f < 0.0;
   fse_status st;
   if (P->dim == 2) {
-    m.lp = 0;
-    m.lr = P->ny;
-    m.dkr = 2 * kPi / (P->p.hi[1] - P->p.lo[1]);
     m.scale = 1.0 / ((double)P->nx * P->ny);
     ColArgs a{psi, 0, P->nx, 1, P->nx, P->ny, P->ny, tiles(P, P->ny, P->nx)};
     return col(P, FSE_PASS_KIN, P->ny, 1, -1, a, m);
   }
   ColArgs ay{psi, (long long)P->nx * P->ny, P->nx, P->nz, P->nx, P->ny, P->ny, tiles(P, P->ny, P->nx)};
   if ((st = col(P, FSE_PASS_COL, P->ny, 0, -1, ay, m)) != FSE_OK) return st;
-  m.lp = P->ny;
-  m.dkp = 2 * kPi / (P->p.hi[1] - P->p.lo[1]);
-  m.lr = P->nz;
-  m.dkr = 2 * kPi / (P->p.hi[2] - P->p.lo[2]);
   m.scale = 1.0 / ((double)P->nx * P->ny * P->nz);
   ColArgs az{psi, P->nx, (long long)P->nx * P->ny, P->ny, P->nx, P->nz, P->nz, tiles(P, P->nz, P->nx)};
   if ((st = col(P, FSE_PASS_KIN, P->nz, 1, -1, az, m)) != FSE_OK) return st;
@@ -493,6 +493,11 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
   P->off_chat = off;
   const size_t nchat = (size_t)(P->nx + 1) * (P->ny + 1) * (p.dim == 3 ? P->nz + 1 : 1);
   off = align256(off + nchat * P->rsize);
+  const size_t psi_elems = (size_t)P->nx * P->ny * P->nz;
+  P->off_kin_half = off;
+  off = align256(off + psi_elems * P->csize);
+  P->off_kin_full = off;
+  off = align256(off + psi_elems * P->csize);
   P->off_spec = off;
   const size_t spec_rows = (size_t)(p.dim == 3 ? P->nz * 2 * P->ny : P->ny);
   const size_t spec_bytes = spec_rows * P->sx * P->csize;
@@ -549,6 +554,18 @@ fse_status fse_kernel_precompute(fse_plan_t P) {
     e = P->prec == FSE_F32 ? launch_twiddles<float>(P->ws_ptr(P->tw_off[i]), P->tw_len[i], P->stream)
                            : launch_twiddles<double>(P->ws_ptr(P->tw_off[i]), P->tw_len[i], P->stream);
     if (launched(P, e, "twiddles") != FSE_OK) return FSE_ERR_CUDA;
+  }
+  {
+    const double dk[3] = {2 * kPi / (P->p.hi[0] - P->p.lo[0]), 2 * kPi / (P->p.hi[1] - P->p.lo[1]),
+                          P->dim == 3 ? 2 * kPi / (P->p.hi[2] - P->p.lo[2]) : 0.0};
+    void* kh = P->ws_ptr(P->off_kin_half);
+    void* kf = P->ws_ptr(P->off_kin_full);
+    e = P->prec == FSE_F32
+            ? launch_kin_table<float>(kh, kf, P->nx, P->ny, P->nz, dk[0], dk[1], dk[2], P->p.s, P->p.m * P->p.m,
+                                      P->p.dt, P->stream)
+            : launch_kin_table<double>(kh, kf, P->nx, P->ny, P->nz, dk[0], dk[1], dk[2], P->p.s, P->p.m * P->p.m,
+                                       P->p.dt, P->stream);
+    if (launched(P, e, "kinetic tables") != FSE_OK) return FSE_ERR_CUDA;
   }
   if (P->p.kernel != FSE_KERNEL_NONE) {
     char* base = reinterpret_cast<char*>(P->ws_ptr(P->off_spec));

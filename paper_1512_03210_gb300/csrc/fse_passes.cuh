@@ -32,7 +32,16 @@ __host__ __device__ constexpr int ncol_for(int N, int csize) {
   while (n > 2 && n * N * csize > 65536) n /= 2;
   return n;
 }
-__host__ __device__ constexpr int nt_for(int N, int ncol) { return N * ncol >= 4096 ? 256 : 128; }
+// Threads per tile: about 16 elements per thread, so that a Stockham pass holds
+// at most two radix-8 butterflies in registers per thread.
+__host__ __device__ constexpr int nt_for(int N, int ncol) {
+  return N * ncol >= 4096 ? 512 : (N * ncol >= 2048 ? 256 : 128);
+}
+// Resident tiles per SM the register budget is sized for: 64 registers per
+// thread for float (1024 threads per SM), 128 for double (512 threads).
+__host__ __device__ constexpr int minb_for(int nt, int csize) {
+  return (csize == 8 ? 1024 : 512) / nt > 0 ? (csize == 8 ? 1024 : 512) / nt : 1;
+}
 
 struct ColArgs {
   void* data;
@@ -55,6 +64,8 @@ struct MulArgs {
   double q[6];       // DDI: 3*scale*(Mxx, Myy, Mrr..): see host code (x, plane, row)
   const void* chat;
   long long chat_sp, chat_sr;
+  const void* kin;   // kinetic: table of exp(-i f theta_k) in the field's layout
+  int conj;          // kinetic: multiply by the conjugate of the table (adjoint)
 };
 
 struct XArgs {
@@ -96,7 +107,8 @@ __device__ __forceinline__ int wrap_index(int i, int L) { return i < (L >> 1) ? 
 // MODE 2: fwd . kernel transform . inv (Coulomb or 3D DDI, chosen in MulArgs).
 // ---------------------------------------------------------------------------
 template <typename Real, int N, int MODE, int DIR>
-__global__ void __launch_bounds__(nt_for(N, ncol_for(N, 2 * sizeof(Real))))
+__global__ void __launch_bounds__(nt_for(N, ncol_for(N, 2 * sizeof(Real))),
+                                  minb_for(nt_for(N, ncol_for(N, 2 * sizeof(Real))), 2 * sizeof(Real)))
 k_colpass(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__ tw) {
   typedef typename Cplx<Real>::T C;
   constexpr int NCOL = ncol_for(N, sizeof(C));
@@ -112,7 +124,7 @@ k_colpass(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__ tw) {
   C* base = reinterpret_cast<C*>(a.data) + (long long)plane * a.plane_stride + c0;
   const int ncv = min(NCOL, a.ncols - c0);
 
-#pragma unroll
+#pragma unroll 8
   for (int it = 0; it < PER; ++it) {
     const int idx = tid + it * NT;
     if ((TOT % NT) == 0 || idx < TOT) {
@@ -127,7 +139,7 @@ k_colpass(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__ tw) {
     fft_tile<C, N, NCOL, NT, DIR>(buf, tw);
   } else {
     fft_tile<C, N, NCOL, NT, -1>(buf, tw);
-#pragma unroll
+#pragma unroll 4
     for (int it = 0; it < PER; ++it) {
       const int idx = tid + it * NT;
       if ((TOT % NT) == 0 || idx < TOT) {
@@ -136,18 +148,13 @@ k_colpass(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__ tw) {
         C v = buf[j * LDS + c];
         const int pr = wrap_index(j, m.lr);
         if constexpr (MODE == 1) {
-          const int px = wrap_index(ix, m.lx);
-          const Real kx = Real(m.dkx) * Real(px), kr = Real(m.dkr) * Real(pr);
-          Real k2 = kx * kx + kr * kr + Real(m.m2);
-          if (m.lp) {
-            const Real kp = Real(m.dkp) * Real(wrap_index(plane, m.lp));
-            k2 += kp * kp;
-          }
-          const Real th = Real(m.c0) * pow(k2, Real(m.s));
-          Real sn, cs;
-          sincos(th, &sn, &cs);
+          // kinetic phase exp(-i f theta_k) from the plan's table (same layout as the field)
+          const C* tab = reinterpret_cast<const C*>(m.kin);
+          const C t = c < ncv ? __ldg(&tab[(long long)plane * a.plane_stride + c0 + c + (long long)j * a.line_stride])
+                              : mk(Real(0), Real(0));
           const Real sc = Real(m.scale);
-          v = mk(sc * (v.x * cs + v.y * sn), sc * (v.y * cs - v.x * sn));
+          v = m.conj ? cmulc(v, t) : cmul(v, t);
+          v = mk(sc * v.x, sc * v.y);
         } else {
           // kernel transform on the padded grid; x index is an R2C bin 0..nx
           const int px = ix;                                   // non-negative
@@ -178,7 +185,7 @@ k_colpass(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__ tw) {
     __syncthreads();
     fft_tile<C, N, NCOL, NT, +1>(buf, tw);
   }
-#pragma unroll
+#pragma unroll 8
   for (int it = 0; it < PER; ++it) {
     const int idx = tid + it * NT;
     if ((TOT % NT) == 0 || idx < TOT) {
@@ -294,7 +301,7 @@ __device__ __forceinline__ Real trap_phase(const XArgs& a, int x, int lg) {
 }
 
 template <typename Real, int NX, int KIND>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, sizeof(Real) == 4 ? 4 : 2)
 k_xpass(XArgs a, const typename Cplx<Real>::T* __restrict__ twn,
         const typename Cplx<Real>::T* __restrict__ tw2n) {
   typedef XCfg<Real, NX> K;
@@ -308,7 +315,7 @@ k_xpass(XArgs a, const typename Cplx<Real>::T* __restrict__ twn,
   C* psi = reinterpret_cast<C*>(a.psi);
 
   if constexpr (KIND == XP_FWD || KIND == XP_INV || KIND == XP_E) {
-#pragma unroll
+#pragma unroll 8
     for (int it = 0; it < PER; ++it) {
       const int idx = tid + it * NT;
       if ((TOT % NT) == 0 || idx < TOT) {
@@ -467,7 +474,7 @@ k_xpass(XArgs a, const typename Cplx<Real>::T* __restrict__ twn,
       }
       __syncthreads();
       fft_tile<C, NX, NCOL, NT, -1>(buf, twn);
-#pragma unroll
+#pragma unroll 8
       for (int it = 0; it < PER; ++it) {
         const int idx = tid + it * NT;
         if ((TOT % NT) == 0 || idx < TOT) {

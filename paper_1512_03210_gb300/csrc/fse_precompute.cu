@@ -46,6 +46,44 @@ __global__ void k_twiddles(typename Cplx<Real>::T* tw, int L) {
   round_pair(c, s, &tw[m]);
 }
 
+// Kinetic multipliers exp(-i theta_k) (half step, theta = dt/4 (|k|^2+m^2)^s)
+// and exp(-2 i theta_k) (two merged half steps) in the field's layout
+// [nz][ny][nx] with wrapped mode numbers; float64 arithmetic, rounded to the
+// plan's precision with the norm-closest float pair (see round_pair).
+template <typename Real>
+__global__ void k_kin_table(typename Cplx<Real>::T* half, typename Cplx<Real>::T* full, int nx, int ny, int nz,
+                            double dkx, double dky, double dkz, double s, double m2, double dt) {
+  const long long N = (long long)nx * ny * nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(i % nx);
+    const long long r = i / nx;
+    const int iy = (int)(r % ny), iz = (int)(r / ny);
+    const double kx = dkx * (ix < nx / 2 ? ix : ix - nx);
+    const double ky = dky * (iy < ny / 2 ? iy : iy - ny);
+    const double kz = nz > 1 ? dkz * (iz < nz / 2 ? iz : iz - nz) : 0.0;
+    const double k2 = kx * kx + ky * ky + kz * kz + m2;
+    const double th = 0.25 * dt * (k2 > 0.0 ? pow(k2, s) : 0.0);
+    double sn, cs;
+    sincos(th, &sn, &cs);
+    round_pair(cs, -sn, &half[i]);
+    sincos(2.0 * th, &sn, &cs);
+    round_pair(cs, -sn, &full[i]);
+  }
+}
+
+template <typename Real>
+cudaError_t launch_kin_table(void* half, void* full, int nx, int ny, int nz, double dkx, double dky, double dkz,
+                             double s, double m2, double dt, cudaStream_t st) {
+  k_kin_table<Real><<<1024, 256, 0, st>>>(reinterpret_cast<typename Cplx<Real>::T*>(half),
+                                          reinterpret_cast<typename Cplx<Real>::T*>(full), nx, ny, nz, dkx, dky,
+                                          dkz, s, m2, dt);
+  return cudaGetLastError();
+}
+template cudaError_t launch_kin_table<float>(void*, void*, int, int, int, double, double, double, double, double,
+                                             double, cudaStream_t);
+template cudaError_t launch_kin_table<double>(void*, void*, int, int, int, double, double, double, double, double,
+                                              double, cudaStream_t);
+
 // Quadrature nodes on [0, W]: npan panels of ngl Gauss-Legendre points.
 // cs[y * (n+1) + p] = cos(k_p y_y); e[qw * ny + y] = w_y exp(-tau_q^2 y_y^2) for the wide q.
 __global__ void k_gs_cos(double* cs, const double* glx, const double* glw, int ngl, int npan,
