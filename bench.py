@@ -240,6 +240,7 @@ def main():
     ap.add_argument("--f64-steps", type=int, default=40)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--oracle-steps", type=int, default=1)
+    ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -359,6 +360,32 @@ def main():
                "h2d_bytes_per_step": int(host.nbytes), "d2h_bytes_per_step": int(host.nbytes),
                "calls": args.e2e_steps, "note": "one fse_step_host call (1 split step) per step"}
 
+    # batched 2D workload: 256 independent runs of mixed sizes advanced together
+    batched = None
+    if args.batched_steps > 0:
+        runs = I.batched_runs()
+        bt = fse.Batch(runs, stream=stream, device=dev)
+        xs = bt.to_device([I.psi0(r) for r in runs])
+        bt.step(xs, 0.0, 2)
+        torch.cuda.synchronize(dev)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        lb = bt.launches
+        b0.record(stream)
+        bt.step(xs, 2e-3, args.batched_steps)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        bms = b0.elapsed_time(b1)
+        pts = sum(r["n"][0] * r["n"][1] for r in runs)
+        bb = sum(step_model_bytes(dict(r, prec="f32")) for r in runs)
+        batched = {"workload": "batched_2d", "runs": len(runs), "steps": args.batched_steps,
+                   "run_steps_per_s": len(runs) * args.batched_steps / (bms / 1000.0),
+                   "grid_point_steps_per_s": pts * args.batched_steps / (bms / 1000.0),
+                   "ms_per_batch_step": bms / args.batched_steps, "launches": bt.launches - lb,
+                   "model_bytes_per_batch_step": bb,
+                   "model_frac_of_hbm": bb * args.batched_steps / (bms / 1000.0) / 1e9 / peak,
+                   "sizes": sorted({r["n"][0] for r in runs})}
+        del bt, xs
+
     if rank != 0:
         return 0
     cb = None
@@ -375,7 +402,7 @@ def main():
         "grid_point_steps_per_s": value * 256 ** 3,
         "model_bytes_per_step": step_bytes,
         "step_roofline_frac": step_bytes * value / world / 1e9 / peak,
-        "roofline": roofline, "kernels": kernels, "f64": f64, "e2e": e2e,
+        "roofline": roofline, "kernels": kernels, "f64": f64, "e2e": e2e, "batched_2d": batched,
         "cpu_baseline": cb, "gpu_launches": launches, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

@@ -187,6 +187,39 @@ fse_status fse_plan_profile(fse_plan_t plan, int enable);
  * launches (count[FSE_NPASS]) since the last read; then clear the record. */
 fse_status fse_plan_profile_read(fse_plan_t plan, double* ms, long long* count);
 
+/* ---- Batched 2D runs ------------------------------------------------------
+ * Many independent 2D runs (each the scheme of Section 4.2, Eqs. tssp1-tssp3,
+ * with its own grid size, s, m, Omega, beta, lambda, dt and trap) advanced
+ * together: runs of equal grid size share one launch per pass and one kernel
+ * transform; a run advanced in a batch is bit-identical to the same run
+ * advanced alone with fse_step. Requirements: dim 2, FSE_F32, renormalize 0,
+ * one box and one kernel (none or Coulomb) for the whole batch. */
+typedef struct fse_batch* fse_batch_t;
+
+/* Validate runs[0..nruns), create the batch on cuda_stream and return the
+ * device workspace size it needs. Errors: FSE_ERR_INVALID (null, nruns <= 0,
+ * DDI kernel), FSE_ERR_UNSUPPORTED (a requirement above not met, or a run's
+ * own fse_plan_create error). */
+fse_status fse_batch_create(const fse_params* runs, int nruns, void* cuda_stream, fse_batch_t* out,
+                            size_t* workspace_bytes);
+/* Attach caller-owned device memory (256-byte aligned, at least the size
+ * reported). Errors as fse_plan_set_workspace. */
+fse_status fse_batch_set_workspace(fse_batch_t batch, void* dev_ptr, size_t bytes);
+/* Once per batch: twiddles and Gaussian-sum kernel transform per grid size
+ * (Section 2) and kinetic phase tables per run. Asynchronous. */
+fse_status fse_batch_precompute(fse_batch_t batch);
+/* Advance every run by nsteps steps from t0. psi is a HOST array of nruns
+ * DEVICE pointers, one wave function per run in that run's layout [ny][nx]
+ * (float2). Asynchronous. Errors: FSE_ERR_INVALID (null or misaligned
+ * pointers, precompute not run). */
+fse_status fse_batch_step(fse_batch_t batch, void* const* psi, double t0, int nsteps);
+/* Release the batch's host memory (never the workspace). */
+fse_status fse_batch_destroy(fse_batch_t batch);
+/* Detail of the last error on the batch ("" if none). */
+const char* fse_batch_error(fse_batch_t batch);
+/* Kernel launches issued by the batch since creation. */
+long long fse_batch_launch_count(fse_batch_t batch);
+
 /* Largest npoints accepted by fse_mass_noalloc (4096 partials of 65536 points). */
 #define FSE_NOALLOC_MAX_POINTS (4096LL * 65536LL)
 

@@ -23,7 +23,8 @@ __all__ = [
     "fse_step_host", "fse_step_adjoint", "fse_observables", "fse_plan_set_stream",
     "fse_plan_destroy", "fse_status_string", "fse_plan_error", "fse_plan_launch_count",
     "header_functions", "to_params", "fse_plan_profile", "fse_plan_profile_read", "PASS_KINDS",
-    "fse_mass_noalloc",
+    "fse_mass_noalloc", "Batch", "fse_batch_create", "fse_batch_set_workspace", "fse_batch_precompute",
+    "fse_batch_step", "fse_batch_destroy", "fse_batch_error", "fse_batch_launch_count",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -108,6 +109,13 @@ def load(build_if_missing: bool = True):
         "fse_plan_profile": (ct.c_int, [P, ct.c_int]),
         "fse_plan_profile_read": (ct.c_int, [P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_longlong)]),
         "fse_mass_noalloc": (ct.c_int, [P, ct.c_int, ct.c_longlong, ct.c_double, P, P]),
+        "fse_batch_create": (ct.c_int, [ct.POINTER(FseParams), ct.c_int, P, ct.POINTER(P), ct.POINTER(ct.c_size_t)]),
+        "fse_batch_set_workspace": (ct.c_int, [P, P, ct.c_size_t]),
+        "fse_batch_precompute": (ct.c_int, [P]),
+        "fse_batch_step": (ct.c_int, [P, ct.POINTER(P), ct.c_double, ct.c_int]),
+        "fse_batch_destroy": (ct.c_int, [P]),
+        "fse_batch_error": (ct.c_char_p, [P]),
+        "fse_batch_launch_count": (ct.c_longlong, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -262,6 +270,82 @@ def fse_plan_error(plan) -> str:
 
 def fse_plan_launch_count(plan) -> int:
     return int(load().fse_plan_launch_count(plan))
+
+
+def _bcheck(st: int, where: str, batch=None):
+    if st != FSE_OK:
+        detail = load().fse_batch_error(batch).decode() if batch else ""
+        raise FseError(st, where, detail)
+
+
+def fse_batch_create(runs: list, stream=None):
+    """Returns (batch handle, workspace bytes) for a list of 2D parameter dicts."""
+    arr = (FseParams * len(runs))(*[to_params(r) for r in runs])
+    h = ct.c_void_p()
+    nb = ct.c_size_t()
+    _bcheck(load().fse_batch_create(arr, len(runs), ct.c_void_p(stream or 0), ct.byref(h), ct.byref(nb)),
+            "fse_batch_create")
+    return h, nb.value
+
+
+def fse_batch_set_workspace(batch, ws, nbytes: int):
+    _bcheck(load().fse_batch_set_workspace(batch, _ptr(ws), nbytes), "fse_batch_set_workspace", batch)
+
+
+def fse_batch_precompute(batch):
+    _bcheck(load().fse_batch_precompute(batch), "fse_batch_precompute", batch)
+
+
+def fse_batch_step(batch, psis: list, t0: float, nsteps: int):
+    arr = (ct.c_void_p * len(psis))(*[x.data_ptr() for x in psis])
+    _bcheck(load().fse_batch_step(batch, arr, float(t0), int(nsteps)), "fse_batch_step", batch)
+
+
+def fse_batch_destroy(batch):
+    load().fse_batch_destroy(batch)
+
+
+def fse_batch_error(batch) -> str:
+    return load().fse_batch_error(batch).decode()
+
+
+def fse_batch_launch_count(batch) -> int:
+    return int(load().fse_batch_launch_count(batch))
+
+
+class Batch:
+    """Independent 2D runs advanced together, with a torch-allocated workspace."""
+
+    def __init__(self, runs: list, stream=None, device=None):
+        import torch
+        self.runs = [dict(r) for r in runs]
+        self.device = torch.device(device or "cuda")
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        with torch.cuda.device(self.device):
+            self.handle, self.ws_bytes = fse_batch_create(self.runs, stream.cuda_stream)
+            self.ws = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=self.device)
+            fse_batch_set_workspace(self.handle, self.ws, self.ws_bytes)
+            fse_batch_precompute(self.handle)
+
+    def to_device(self, psis: list) -> list:
+        import torch
+        return [torch.as_tensor(np.ascontiguousarray(p)).to(self.device, torch.complex64).contiguous() for p in psis]
+
+    def step(self, psis: list, t0: float, nsteps: int):
+        fse_batch_step(self.handle, psis, t0, nsteps)
+        return psis
+
+    @property
+    def launches(self) -> int:
+        return fse_batch_launch_count(self.handle)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.fse_batch_destroy(h)
+            self.handle = None
 
 
 class Plan:

@@ -207,12 +207,12 @@ void prof_end(fse_plan* P, int kind, cudaEvent_t a) {
   P->recs.push_back({kind, a, b});
 }
 
-fse_status col(fse_plan* P, int kind, int N, int mode, int dir, const ColArgs& a, const MulArgs& m) {
+fse_status col(fse_plan* P, int kind, int N, int var, const ColArgs& a, const MulArgs& m) {
   if (!twiddle(P, N)) return fail(P, FSE_ERR_INVALID, "no twiddle table for a column pass length");
   cudaEvent_t ev = prof_begin(P);
   cudaError_t e = P->prec == FSE_F32
-                      ? launch_colpass<float>(N, mode, dir, a, m, twiddle(P, N), P->stream)
-                      : launch_colpass<double>(N, mode, dir, a, m, twiddle(P, N), P->stream);
+                      ? launch_colpass<float>(N, var, a, m, twiddle(P, N), P->stream)
+                      : launch_colpass<double>(N, var, a, m, twiddle(P, N), P->stream);
   prof_end(P, kind, ev);
   return launched(P, e, "column pass");
 }
@@ -273,14 +273,14 @@ fse_status kinetic_yz(fse_plan* P, void* psi, double f, double dt) {
   if (P->dim == 2) {
     m.scale = 1.0 / ((double)P->nx * P->ny);
     ColArgs a{psi, 0, P->nx, 1, P->nx, P->ny, P->ny, tiles(P, P->ny, P->nx)};
-    return col(P, FSE_PASS_KIN, P->ny, 1, -1, a, m);
+    return col(P, FSE_PASS_KIN, P->ny, COL_KIN, a, m);
   }
   ColArgs ay{psi, (long long)P->nx * P->ny, P->nx, P->nz, P->nx, P->ny, P->ny, tiles(P, P->ny, P->nx)};
-  if ((st = col(P, FSE_PASS_COL, P->ny, 0, -1, ay, m)) != FSE_OK) return st;
+  if ((st = col(P, FSE_PASS_COL, P->ny, COL_FWD, ay, m)) != FSE_OK) return st;
   m.scale = 1.0 / ((double)P->nx * P->ny * P->nz);
   ColArgs az{psi, P->nx, (long long)P->nx * P->ny, P->ny, P->nx, P->nz, P->nz, tiles(P, P->nz, P->nx)};
-  if ((st = col(P, FSE_PASS_KIN, P->nz, 1, -1, az, m)) != FSE_OK) return st;
-  return col(P, FSE_PASS_COL, P->ny, 0, +1, ay, m);
+  if ((st = col(P, FSE_PASS_KIN, P->nz, COL_KIN, az, m)) != FSE_OK) return st;
+  return col(P, FSE_PASS_COL, P->ny, COL_INV, ay, m);
 }
 
 // Padded forward transform along y (and z), kernel multiplier, inverse and crop
@@ -306,11 +306,11 @@ fse_status nonlocal_yz(fse_plan* P, void* spec, double ta, double tb, bool integ
     m.scale = extra_scale / (4.0 * P->nx * P->ny);
     m.a0 = d * m.scale;
     ColArgs a{spec, 0, P->sx, 1, P->nx + 1, P->ny, P->ny, tiles(P, 2 * P->ny, P->nx + 1)};
-    return col(P, FSE_PASS_KHAT, 2 * P->ny, 2, -1, a, m);
+    return col(P, FSE_PASS_KHAT, 2 * P->ny, COL_KHAT, a, m);
   }
   ColArgs af{spec, (long long)2 * P->ny * P->sx, P->sx, P->nz, P->nx + 1, P->ny, 2 * P->ny,
              tiles(P, 2 * P->ny, P->nx + 1)};
-  if ((st = col(P, FSE_PASS_PAD, 2 * P->ny, 0, -1, af, m)) != FSE_OK) return st;
+  if ((st = col(P, FSE_PASS_PAD, 2 * P->ny, COL_PADF, af, m)) != FSE_OK) return st;
   m.lp = 2 * P->ny;
   m.dkp = 2 * kPi / (2.0 * (P->p.hi[1] - P->p.lo[1]));
   m.lr = 2 * P->nz;
@@ -337,10 +337,10 @@ fse_status nonlocal_yz(fse_plan* P, void* spec, double ta, double tb, bool integ
   }
   ColArgs ag{spec, P->sx, (long long)2 * P->ny * P->sx, 2 * P->ny, P->nx + 1, P->nz, P->nz,
              tiles(P, 2 * P->nz, P->nx + 1)};
-  if ((st = col(P, FSE_PASS_KHAT, 2 * P->nz, 2, -1, ag, m)) != FSE_OK) return st;
+  if ((st = col(P, FSE_PASS_KHAT, 2 * P->nz, COL_KHAT, ag, m)) != FSE_OK) return st;
   ColArgs ah{spec, (long long)2 * P->ny * P->sx, P->sx, P->nz, P->nx + 1, 2 * P->ny, P->ny,
              tiles(P, 2 * P->ny, P->nx + 1)};
-  return col(P, FSE_PASS_PAD, 2 * P->ny, 0, +1, ah, m);
+  return col(P, FSE_PASS_PAD, 2 * P->ny, COL_CROPI, ah, m);
 }
 
 bool has_nonlocal(const fse_plan* P) { return P->p.kernel != FSE_KERNEL_NONE && P->p.lambda != 0.0; }
@@ -488,7 +488,7 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
     if (seen) continue;
     P->tw_len.push_back(lens[i]);
     P->tw_off.push_back(off);
-    off = align256(off + (size_t)lens[i] * P->csize);
+    off = align256(off + 2 * (size_t)lens[i] * P->csize);  // (cos, sin) and modulus correction
   }
   P->off_chat = off;
   const size_t nchat = (size_t)(P->nx + 1) * (P->ny + 1) * (p.dim == 3 ? P->nz + 1 : 1);

@@ -1,0 +1,358 @@
+// fse_batch.cu -- many independent 2D TS2-GauSum runs advanced together.
+//
+// Runs with the same grid size form a group. Every pass of the split step
+// (Section 4.2, Eqs. tssp1-tssp3) is one launch per group: blockIdx.x walks
+// the tiles of one run, blockIdx.y selects the run, whose buffers and
+// parameters (s through its kinetic tables, Omega, beta, lambda, dt, gamma)
+// come from a device descriptor table. The pass bodies are the single-run
+// ones, so a run advanced in a batch is bit-identical to the same run
+// advanced alone. Runs never wait on one another.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fse.h"
+#include "fse_internal.h"
+#include "fse_launch.cuh"
+
+namespace fse {
+
+struct BatchRun {
+  void* psi;
+  void* spec;
+  const void* kin_half;
+  const void* kin_full;
+  double beta, lam, dt, omega, gx2, gy2;
+};
+
+__device__ __forceinline__ double sin_over_dev(double a, double d) {
+  const double z = a * d;
+  return fabs(z) < 1e-6 ? d * (1.0 - z * z / 6.0) : sin(z) / a;
+}
+
+template <typename Real, int N, int VAR>
+__global__ void __launch_bounds__(ColCfg<Real, N>::NT, ColCfg<Real, N>::MINB)
+k_colpass_batch(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__ tw, const BatchRun* runs,
+                int on_spec, int kin_full, int conj) {
+  const BatchRun r = runs[blockIdx.y];
+  a.data = on_spec ? r.spec : r.psi;
+  if constexpr (VAR == COL_KIN) {
+    m.kin = kin_full ? r.kin_full : r.kin_half;
+    m.conj = conj;
+  } else {
+    m.a0 = r.dt * m.scale;
+  }
+  colpass_body<Real, N, VAR>(a, m, tw, blockIdx.x);
+}
+
+template <typename Real, int NX, int KIND>
+__global__ void __launch_bounds__(XCfg<Real, NX>::NT, XCfg<Real, NX>::MINB)
+k_xpass_batch(XArgs a, const typename Cplx<Real>::T* __restrict__ twn, const typename Cplx<Real>::T* __restrict__ tw2n,
+              const BatchRun* runs, double t0, int step) {
+  const BatchRun r = runs[blockIdx.y];
+  a.psi = r.psi;
+  a.spec = a.use_spec ? r.spec : nullptr;
+  if constexpr (KIND == XP_A) {
+    // exact time integral of the rotating harmonic trap over the run's step (Eq. int_poten)
+    const double ta = t0 + step * r.dt, d = r.dt, mid = 2.0 * ta + d;
+    const double C2 = cos(r.omega * mid) * sin_over_dev(r.omega, d);
+    const double S2 = sin(r.omega * mid) * sin_over_dev(r.omega, d);
+    a.pa = 0.25 * (r.gx2 * (d + C2) + r.gy2 * (d - C2));
+    a.pb = 0.25 * (r.gx2 * (d - C2) + r.gy2 * (d + C2));
+    a.pc = 0.5 * (r.gx2 - r.gy2) * S2;
+    a.pe = 0.0;
+    a.beta_dt = r.beta * r.dt;
+    a.lam = r.lam;
+  }
+  xpass_body<Real, NX, KIND>(a, twn, tw2n, blockIdx.x);
+}
+
+template <int N, int VAR>
+static cudaError_t colb(const ColArgs& a, const MulArgs& m, const void* tw, const BatchRun* runs, int nr,
+                        int on_spec, int kin_full, int conj, cudaStream_t st) {
+  typedef ColCfg<float, N> K;
+  const size_t smem = K::smem_bytes(VAR);
+  static std::atomic<unsigned long long> done{0};
+  cudaError_t e = allow_smem(k_colpass_batch<float, N, VAR>, smem, done);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.nplanes * a.tiles_per_plane, nr);
+  k_colpass_batch<float, N, VAR><<<grid, K::NT, smem, st>>>(a, m, reinterpret_cast<const float2*>(tw), runs, on_spec,
+                                                             kin_full, conj);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_colb(int N, int mode, const ColArgs& a, const MulArgs& m, const void* tw,
+                               const BatchRun* runs, int nr, int on_spec, int kin_full, int conj, cudaStream_t st) {
+  switch (N) {
+#define FSE_CASE(n)                                                                          \
+  case n:                                                                                    \
+    return mode == 1 ? colb<n, COL_KIN>(a, m, tw, runs, nr, on_spec, kin_full, conj, st)      \
+                     : colb<n, COL_KHAT>(a, m, tw, runs, nr, on_spec, kin_full, conj, st);
+    FSE_COL_SIZES(FSE_CASE)
+#undef FSE_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <int NX, int KIND>
+static cudaError_t xb(const XArgs& a, const void* twn, const void* tw2n, const BatchRun* runs, int nr, double t0,
+                      int step, cudaStream_t st) {
+  typedef XCfg<float, NX> K;
+  const size_t smem = K::smem_bytes();
+  static std::atomic<unsigned long long> done{0};
+  cudaError_t e = allow_smem(k_xpass_batch<float, NX, KIND>, smem, done);
+  if (e != cudaSuccess) return e;
+  dim3 grid((a.nlines + K::NCOL - 1) / K::NCOL, nr);
+  k_xpass_batch<float, NX, KIND><<<grid, K::NT, smem, st>>>(a, reinterpret_cast<const float2*>(twn),
+                                                            reinterpret_cast<const float2*>(tw2n), runs, t0, step);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_xb(int kind, int nx, const XArgs& a, const void* twn, const void* tw2n,
+                             const BatchRun* runs, int nr, double t0, int step, cudaStream_t st) {
+  switch (nx) {
+#define FSE_CASE(n)                                                    \
+  case n:                                                              \
+    switch (kind) {                                                    \
+      case XP_FWD: return xb<n, XP_FWD>(a, twn, tw2n, runs, nr, t0, step, st); \
+      case XP_INV: return xb<n, XP_INV>(a, twn, tw2n, runs, nr, t0, step, st); \
+      case XP_E: return xb<n, XP_E>(a, twn, tw2n, runs, nr, t0, step, st);     \
+      default: return xb<n, XP_A>(a, twn, tw2n, runs, nr, t0, step, st);       \
+    }
+    FSE_X_SIZES(FSE_CASE)
+#undef FSE_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+const void* twiddle(const fse_plan* P, int L);
+template <typename Real>
+cudaError_t launch_kin_table(void* half, void* full, int nx, int ny, int nz, double dkx, double dky, double dkz,
+                             double s, double m2, double dt, cudaStream_t st);
+
+}  // namespace fse
+
+using namespace fse;
+
+struct fse_batch {
+  struct Group {
+    int nx = 0, ny = 0;
+    std::vector<int> runs;
+    fse_plan* plan = nullptr;  // twiddles and kernel transform of the group (shared by its runs)
+    size_t off_plan = 0, off_desc = 0;
+  };
+  std::vector<fse_params> runs;
+  std::vector<Group> groups;
+  std::vector<size_t> off_kh, off_kf, off_spec;
+  cudaStream_t stream = nullptr;
+  size_t ws_bytes = 0;
+  void* ws = nullptr;
+  bool precomputed = false;
+  long long launches = 0;
+  std::string err;
+  std::vector<BatchRun> desc;  // host staging of the descriptor tables
+  char* ptr(size_t off) const { return static_cast<char*>(ws) + off; }
+};
+
+namespace {
+size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+fse_status bfail(fse_batch* B, fse_status st, const std::string& m) {
+  B->err = m;
+  return st;
+}
+}  // namespace
+
+extern "C" {
+
+fse_status fse_batch_create(const fse_params* runs, int nruns, void* stream, fse_batch_t* out,
+                            size_t* workspace_bytes) {
+  if (!runs || nruns <= 0 || !out || !workspace_bytes) return FSE_ERR_INVALID;
+  *out = nullptr;
+  *workspace_bytes = 0;
+  for (int r = 0; r < nruns; ++r) {
+    const fse_params& p = runs[r];
+    if (p.dim != 2 || p.prec != FSE_F32 || p.renormalize != 0) return FSE_ERR_UNSUPPORTED;
+    if (p.kernel == FSE_KERNEL_DDI3D) return FSE_ERR_INVALID;
+    if (p.lo[0] != runs[0].lo[0] || p.lo[1] != runs[0].lo[1] || p.hi[0] != runs[0].hi[0] ||
+        p.hi[1] != runs[0].hi[1] || p.kernel != runs[0].kernel)
+      return FSE_ERR_UNSUPPORTED;  // one box and one kernel per batch
+  }
+  fse_batch* B = new (std::nothrow) fse_batch();
+  if (!B) return FSE_ERR_NOMEM;
+  B->runs.assign(runs, runs + nruns);
+  B->stream = reinterpret_cast<cudaStream_t>(stream);
+  for (int r = 0; r < nruns; ++r) {
+    int g = -1;
+    for (size_t k = 0; k < B->groups.size(); ++k)
+      if (B->groups[k].nx == runs[r].n[0] && B->groups[k].ny == runs[r].n[1]) g = (int)k;
+    if (g < 0) {
+      B->groups.emplace_back();
+      g = (int)B->groups.size() - 1;
+      B->groups[g].nx = runs[r].n[0];
+      B->groups[g].ny = runs[r].n[1];
+    }
+    B->groups[g].runs.push_back(r);
+  }
+  size_t off = 0;
+  B->off_kh.assign(nruns, 0);
+  B->off_kf.assign(nruns, 0);
+  B->off_spec.assign(nruns, 0);
+  for (auto& G : B->groups) {
+    size_t nb = 0;
+    fse_status st = fse_plan_create(&runs[G.runs[0]], stream, &G.plan, &nb);
+    if (st != FSE_OK) {
+      fse_batch_destroy(B);
+      return st;
+    }
+    G.off_plan = off;
+    off = al(off + nb);
+    G.off_desc = off;
+    off = al(off + sizeof(BatchRun) * G.runs.size());
+    const size_t psi_bytes = (size_t)G.nx * G.ny * 8;
+    const size_t spec_bytes = (size_t)G.ny * G.plan->sx * 8;
+    for (size_t k = 1; k < G.runs.size(); ++k) {
+      const int r = G.runs[k];
+      B->off_kh[r] = off;
+      off = al(off + psi_bytes);
+      B->off_kf[r] = off;
+      off = al(off + psi_bytes);
+      B->off_spec[r] = off;
+      off = al(off + spec_bytes);
+    }
+  }
+  B->ws_bytes = off;
+  *workspace_bytes = off;
+  *out = B;
+  return FSE_OK;
+}
+
+fse_status fse_batch_set_workspace(fse_batch_t B, void* ptr, size_t bytes) {
+  if (!B || !ptr) return FSE_ERR_INVALID;
+  if (reinterpret_cast<uintptr_t>(ptr) % 256 != 0) return bfail(B, FSE_ERR_INVALID, "workspace not 256-byte aligned");
+  if (bytes < B->ws_bytes) return bfail(B, FSE_ERR_NOMEM, "workspace smaller than fse_batch_create reported");
+  B->ws = ptr;
+  B->precomputed = false;
+  for (auto& G : B->groups) {
+    fse_status st = fse_plan_set_workspace(G.plan, B->ptr(G.off_plan), G.plan->ws_bytes);
+    if (st != FSE_OK) return bfail(B, st, G.plan->err);
+  }
+  return FSE_OK;
+}
+
+fse_status fse_batch_precompute(fse_batch_t B) {
+  if (!B) return FSE_ERR_INVALID;
+  if (!B->ws) return bfail(B, FSE_ERR_INVALID, "no workspace attached");
+  for (auto& G : B->groups) {
+    fse_status st = fse_kernel_precompute(G.plan);
+    if (st != FSE_OK) return bfail(B, st, G.plan->err);
+    B->launches += G.plan->launches;
+    G.plan->launches = 0;
+    for (size_t k = 1; k < G.runs.size(); ++k) {
+      const fse_params& p = B->runs[G.runs[k]];
+      const double dkx = 2 * kPi / (p.hi[0] - p.lo[0]), dky = 2 * kPi / (p.hi[1] - p.lo[1]);
+      cudaError_t e = launch_kin_table<float>(B->ptr(B->off_kh[G.runs[k]]), B->ptr(B->off_kf[G.runs[k]]), G.nx, G.ny,
+                                              1, dkx, dky, 0.0, p.s, p.m * p.m, p.dt, B->stream);
+      if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("kinetic tables: ") + cudaGetErrorString(e));
+      ++B->launches;
+    }
+  }
+  B->precomputed = true;
+  return FSE_OK;
+}
+
+fse_status fse_batch_step(fse_batch_t B, void* const* psi, double t0, int nsteps) {
+  if (!B || !psi || nsteps < 0) return FSE_ERR_INVALID;
+  if (!B->ws || !B->precomputed) return bfail(B, FSE_ERR_INVALID, "fse_batch_precompute has not run");
+  for (size_t r = 0; r < B->runs.size(); ++r)
+    if (!psi[r] || reinterpret_cast<uintptr_t>(psi[r]) % 8 != 0) return bfail(B, FSE_ERR_INVALID, "bad psi pointer");
+  if (nsteps == 0) return FSE_OK;
+  cudaStream_t st = B->stream;
+  for (auto& G : B->groups) {
+    fse_plan* P = G.plan;
+    const int nr = (int)G.runs.size();
+    // descriptor table of the group
+    B->desc.resize(nr);
+    for (int k = 0; k < nr; ++k) {
+      const int r = G.runs[k];
+      const fse_params& p = B->runs[r];
+      BatchRun d;
+      d.psi = psi[r];
+      d.spec = k == 0 ? P->ws_ptr(P->off_spec) : B->ptr(B->off_spec[r]);
+      d.kin_half = k == 0 ? P->ws_ptr(P->off_kin_half) : B->ptr(B->off_kh[r]);
+      d.kin_full = k == 0 ? P->ws_ptr(P->off_kin_full) : B->ptr(B->off_kf[r]);
+      d.beta = p.beta;
+      d.lam = p.lambda;
+      d.dt = p.dt;
+      d.omega = p.omega;
+      d.gx2 = p.gamma[0] * p.gamma[0];
+      d.gy2 = p.gamma[1] * p.gamma[1];
+      B->desc[k] = d;
+    }
+    BatchRun* ddesc = reinterpret_cast<BatchRun*>(B->ptr(G.off_desc));
+    cudaError_t e = cudaMemcpyAsync(ddesc, B->desc.data(), sizeof(BatchRun) * nr, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("descriptor upload: ") + cudaGetErrorString(e));
+    const bool nl = B->runs[G.runs[0]].kernel != FSE_KERNEL_NONE;
+    XArgs xa = x_args(P, nullptr, nl ? reinterpret_cast<void*>(1) : nullptr);  // pointers come from the table
+    xa.use_spec = nl ? 1 : 0;
+    const void* twn = twiddle(P, P->nx);
+    const void* tw2n = twiddle(P, 2 * P->nx);
+    const int ncx = xpass_ncol<float>(P->nx);
+    (void)ncx;
+    MulArgs mk1;
+    std::memset(&mk1, 0, sizeof(mk1));
+    mk1.mode = MUL_KIN;
+    mk1.scale = 1.0 / ((double)P->nx * P->ny);
+    ColArgs ck{nullptr, 0, P->nx, 1, P->nx, P->ny, P->ny, tiles(P, P->ny, P->nx)};
+    MulArgs mk2;
+    std::memset(&mk2, 0, sizeof(mk2));
+    mk2.mode = MUL_COULOMB;
+    mk2.lx = 2 * P->nx;
+    mk2.lr = 2 * P->ny;
+    mk2.chat = P->ws_ptr(P->off_chat);
+    mk2.chat_sr = P->nx + 1;
+    mk2.scale = 1.0 / (4.0 * P->nx * P->ny);
+    ColArgs cg{nullptr, 0, P->sx, 1, P->nx + 1, P->ny, P->ny, tiles(P, 2 * P->ny, P->nx + 1)};
+    auto chk = [&](cudaError_t ee, const char* w) -> fse_status {
+      if (ee != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string(w) + ": " + cudaGetErrorString(ee));
+      ++B->launches;
+      return FSE_OK;
+    };
+    fse_status s;
+    if ((s = chk(launch_xb(XP_FWD, P->nx, xa, twn, tw2n, ddesc, nr, t0, 0, st), "batch x")) != FSE_OK) return s;
+    for (int n = 0; n < nsteps; ++n) {
+      if ((s = chk(launch_colb(P->ny, 1, ck, mk1, twiddle(P, P->ny), ddesc, nr, 0, n > 0, 0, st), "batch kinetic")) != FSE_OK)
+        return s;
+      if (nl) {
+        if ((s = chk(launch_xb(XP_E, P->nx, xa, twn, tw2n, ddesc, nr, t0, n, st), "batch density")) != FSE_OK) return s;
+        if ((s = chk(launch_colb(2 * P->ny, 2, cg, mk2, twiddle(P, 2 * P->ny), ddesc, nr, 1, 0, 0, st), "batch kernel")) != FSE_OK)
+          return s;
+      } else {
+        if ((s = chk(launch_xb(XP_INV, P->nx, xa, twn, tw2n, ddesc, nr, t0, n, st), "batch x")) != FSE_OK) return s;
+      }
+      if ((s = chk(launch_xb(XP_A, P->nx, xa, twn, tw2n, ddesc, nr, t0, n, st), "batch phase")) != FSE_OK) return s;
+    }
+    if ((s = chk(launch_colb(P->ny, 1, ck, mk1, twiddle(P, P->ny), ddesc, nr, 0, 0, 0, st), "batch kinetic")) != FSE_OK)
+      return s;
+    if ((s = chk(launch_xb(XP_INV, P->nx, xa, twn, tw2n, ddesc, nr, t0, nsteps, st), "batch x")) != FSE_OK) return s;
+  }
+  return FSE_OK;
+}
+
+fse_status fse_batch_destroy(fse_batch_t B) {
+  if (!B) return FSE_OK;
+  for (auto& G : B->groups) fse_plan_destroy(G.plan);
+  delete B;
+  return FSE_OK;
+}
+
+const char* fse_batch_error(fse_batch_t B) { return B ? B->err.c_str() : ""; }
+
+long long fse_batch_launch_count(fse_batch_t B) { return B ? B->launches : 0; }
+
+}  // extern "C"

@@ -2,6 +2,6 @@
 #include "fse_launch.cuh"
 
 namespace fse {
-template cudaError_t launch_colpass<float>(int, int, int, const ColArgs&, const MulArgs&, const void*, cudaStream_t);
+template cudaError_t launch_colpass<float>(int, int, const ColArgs&, const MulArgs&, const void*, cudaStream_t);
 template int colpass_ncol<float>(int);
 }  // namespace fse

@@ -11,8 +11,14 @@
 // The forward transform is unnormalised, X_k = sum_j x_j exp(-2 pi i jk/N);
 // the inverse uses the conjugate twiddles and is also unnormalised (the
 // scale 1/N is applied by the pass that owns the spectral multiplier).
-// Twiddles come from a table tw[m] = exp(-2 pi i m/N) built in float64 and
-// rounded to the plan's precision.
+// Twiddles come from a table holding at tw[2m] the rounded pair w of
+// exp(-2 pi i m/N) (built in float64) and at tw[2m+1] the rounded remainder
+// exp(-2 pi i m/N) - w. Transforms of the wave function (EXACT) multiply by
+// both terms inside one fma chain, so each product is rounded once from a
+// nearly exact twiddle. A rounded pair alone has |w| = 1 + O(1e-8), the same
+// for every element that meets the entry in every step; those fixed gains
+// add up to a steady drift of the norm (about 5e-8 per step in float32).
+// Transforms of the density spectrum (which only sets a phase) use w alone.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -41,6 +47,16 @@ template <typename C> __device__ __forceinline__ C cconj(C a) { return mk(a.x, -
 template <int DIR, typename C> __device__ __forceinline__ C mul_i(C a) {
   return DIR < 0 ? mk(a.y, -a.x) : mk(-a.y, a.x);
 }
+
+// Asynchronous 4/8/16-byte global -> shared copy (cp.async, completes in the
+// background) and the wait for all of a thread's outstanding copies.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------------------
 // Radix plans: N = 2^a 3^b (b <= 1) split into passes of radix 3, 8, 4, 2.
@@ -169,8 +185,55 @@ template <int R, int DIR, typename C> __device__ __forceinline__ void dft(C* v) 
   }
 }
 
+// Error of the modulus of a float pair, c^2 + s^2 - 1, computed exactly enough
+// to correct it: the two squares are split into rounded product plus fma
+// remainder, and the larger square minus one is exact (Sterbenz).
+__device__ __forceinline__ float norm_err(float c, float s) {
+  const bool big = fabsf(c) >= fabsf(s);
+  const float a = big ? c : s, b = big ? s : c;
+  const float pa = a * a, ea = fmaf(a, a, -pa);
+  const float pb = b * b, eb = fmaf(b, b, -pb);
+  return ((pa - 1.0f) + pb) + (ea + eb);
+}
+
+// v times twiddle m of the table (conjugated for the inverse transform).
+// SM: the table sits in shared memory, split into the rounded pairs tw[0..N)
+// followed by the remainders tw[N..2N) (plain loads, consecutive entries on
+// consecutive banks); otherwise it is the interleaved global table.
+template <int DIR, bool EXACT, bool SM = false, int NTW = 0, typename C>
+__device__ __forceinline__ C twiddle_mul(C v, const C* __restrict__ tw, int m) {
+  const C w = SM ? tw[m] : __ldg(&tw[2 * m]);
+  if constexpr (EXACT && sizeof(C) == 8) {
+    const C l = SM ? tw[NTW + m] : __ldg(&tw[2 * m + 1]);
+    if constexpr (DIR < 0) {
+      const float lr = v.x * l.x - v.y * l.y, li = v.x * l.y + v.y * l.x;
+      return mk(fmaf(v.x, w.x, fmaf(-v.y, w.y, lr)), fmaf(v.x, w.y, fmaf(v.y, w.x, li)));
+    } else {
+      const float lr = v.x * l.x + v.y * l.y, li = v.y * l.x - v.x * l.y;
+      return mk(fmaf(v.x, w.x, fmaf(v.y, w.y, lr)), fmaf(-v.x, w.y, fmaf(v.y, w.x, li)));
+    }
+  } else {
+    return DIR < 0 ? cmul(v, w) : cmulc(v, w);
+  }
+}
+
+// v times the float pair (c, s) of a unit-modulus factor, with the pair's
+// modulus error folded into the products before their final rounding (the
+// factor's remainder is taken as -(|w|^2 - 1)/2 w from norm_err).
+__device__ __forceinline__ float2 unit_mul(float2 v, float c, float s, bool conj_w) {
+  const float h = -0.5f * norm_err(c, s);
+  const float lc = h * c, ls = conj_w ? -h * s : h * s;
+  const float sc = conj_w ? -s : s;
+  const float lr = v.x * lc - v.y * ls, li = v.x * ls + v.y * lc;
+  return make_float2(fmaf(v.x, c, fmaf(-v.y, sc, lr)), fmaf(v.x, sc, fmaf(v.y, c, li)));
+}
+__device__ __forceinline__ double2 unit_mul(double2 v, double c, double s, bool conj_w) {
+  const double sc = conj_w ? -s : s;
+  return make_double2(v.x * c - v.y * sc, v.x * sc + v.y * c);
+}
+
 // One Stockham pass of radix R over NCOL lines of length N in shared memory.
-template <typename C, int N, int NCOL, int NT, int DIR, int R, int NS>
+template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, int R, int NS>
 __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) {
   constexpr int LDS = NCOL + 1;
   constexpr int ITEMS = NCOL * (N / R);
@@ -187,10 +250,7 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
       if constexpr (NS > 1) {
         const int k = j % NS;
 #pragma unroll
-        for (int r = 1; r < R; ++r) {
-          C w8 = __ldg(&tw[(k * r) * (N / (NS * R))]);
-          v[it][r] = DIR < 0 ? cmul(v[it][r], w8) : cmulc(v[it][r], w8);
-        }
+        for (int r = 1; r < R; ++r) v[it][r] = twiddle_mul<DIR, EXACT>(v[it][r], tw, (k * r) * (N / (NS * R)));
       }
       dft<R, DIR>(v[it]);
     }
@@ -210,22 +270,178 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
   __syncthreads();
 }
 
-template <typename C, int N, int NCOL, int NT, int DIR, int PASS, int NS>
+template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, int PASS, int NS>
 __device__ __forceinline__ void stockham_rec(C* buf, const C* __restrict__ tw) {
   constexpr RadixPlan P = radix_plan(N);
   if constexpr (PASS < P.npass) {
     constexpr int R = P.r[PASS];
-    stockham_pass<C, N, NCOL, NT, DIR, R, NS>(buf, tw);
-    stockham_rec<C, N, NCOL, NT, DIR, PASS + 1, NS * R>(buf, tw);
+    stockham_pass<C, N, NCOL, NT, DIR, EXACT, R, NS>(buf, tw);
+    stockham_rec<C, N, NCOL, NT, DIR, EXACT, PASS + 1, NS * R>(buf, tw);
   }
 }
 
 // Full transform of NCOL lines of length N held in buf (caller synchronised
 // before the call; the call ends with a barrier).
-template <typename C, int N, int NCOL, int NT, int DIR>
+template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT>
 __device__ __forceinline__ void fft_tile(C* buf, const C* __restrict__ tw) {
   static_assert(fft_size_ok(N), "FFT length must be 2^a or 3*2^a");
-  stockham_rec<C, N, NCOL, NT, DIR, 0, 1>(buf, tw);
+  stockham_rec<C, N, NCOL, NT, DIR, EXACT, 0, 1>(buf, tw);
+}
+
+// ---------------------------------------------------------------------------
+// Register-staged Stockham for column tiles. Each thread owns E elements of the
+// tile in registers (E a multiple of every radix of the plan). Pass p works on
+// items (c, j), j < N/R_p, item i of thread t being w = t + i NT, c = w % NCOL,
+// j = w / NCOL; its inputs are at positions j + r N/R_p and its outputs at
+// (j / Ns) Ns R_p + j % Ns + r Ns. The first pass's inputs come from global
+// memory and the last pass's outputs (positions j + r N/R_last) stay in
+// registers, so a transform of P passes makes P - 1 exchanges through shared
+// memory instead of P + 1.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int plan_lcm(int N) {
+  RadixPlan p = radix_plan(N);
+  int two = 1;
+  bool three = false;
+  for (int i = 0; i < p.npass; ++i) {
+    if (p.r[i] == 3) three = true;
+    else if (p.r[i] > two) two = p.r[i];
+  }
+  return two * (three ? 3 : 1);
+}
+// elements per thread and threads per tile of NCOL lines of length N
+__host__ __device__ constexpr int reg_elems(int N, int ncol) {
+  int e = plan_lcm(N);
+  while (N * ncol / e > 512) e *= 2;
+  return e;
+}
+__host__ __device__ constexpr int reg_threads(int N, int ncol) { return N * ncol / reg_elems(N, ncol); }
+
+template <typename C, int N, int NCOL, int NT, int E, int DIR, bool EXACT, int R, int NS>
+__device__ __forceinline__ void regs_pass(C (&v)[E], const C* __restrict__ tw) {
+  constexpr int I = E / R;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < I; ++i) {
+    const int j = (tid + i * NT) / NCOL;
+    if constexpr (NS > 1) {
+      const int k = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[i * R + r] = twiddle_mul<DIR, EXACT>(v[i * R + r], tw, (k * r) * (N / (NS * R)));
+    }
+    dft<R, DIR>(&v[i * R]);
+  }
+}
+
+template <typename C, int N, int NCOL, int NT, int E, int R, int NS>
+__device__ __forceinline__ void regs_to_smem(const C (&v)[E], C* buf) {
+  constexpr int I = E / R, LDS = NCOL + 1;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < I; ++i) {
+    const int w = tid + i * NT, c = w % NCOL, j = w / NCOL;
+    const int base = (j / NS) * NS * R + j % NS;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[(base + r * NS) * LDS + c] = v[i * R + r];
+  }
+}
+
+template <typename C, int N, int NCOL, int NT, int E, int R>
+__device__ __forceinline__ void smem_to_regs(C (&v)[E], const C* buf) {
+  constexpr int I = E / R, LDS = NCOL + 1;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < I; ++i) {
+    const int w = tid + i * NT, c = w % NCOL, j = w / NCOL;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[i * R + r] = buf[(j + r * (N / R)) * LDS + c];
+  }
+}
+
+// Runs passes PASS..last on v (holding the inputs of pass PASS). On return v
+// holds the outputs of the last pass at positions j + r N/R_last.
+template <typename C, int N, int NCOL, int NT, int E, int DIR, bool EXACT, int PASS, int NS>
+__device__ __forceinline__ void regs_fft(C (&v)[E], C* buf, const C* __restrict__ tw) {
+  constexpr RadixPlan P = radix_plan(N);
+  constexpr int R = P.r[PASS];
+  regs_pass<C, N, NCOL, NT, E, DIR, EXACT, R, NS>(v, tw);
+  if constexpr (PASS + 1 < P.npass) {
+    constexpr int R2 = P.r[PASS + 1];
+    regs_to_smem<C, N, NCOL, NT, E, R, NS>(v, buf);
+    __syncthreads();
+    smem_to_regs<C, N, NCOL, NT, E, R2>(v, buf);
+    __syncthreads();
+    regs_fft<C, N, NCOL, NT, E, DIR, EXACT, PASS + 1, NS * R>(v, buf, tw);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Register-staged Stockham for contiguous lines (the x axis). Item w of a
+// pass of radix R maps to (line l, butterfly j) with j fastest: j = w % (N/R),
+// l = w / (N/R), so the first pass's loads and the last pass's stores touch
+// consecutive addresses. Shared memory holds the NL lines of a tile line by
+// line with one padding slot every 16 elements (lidx), which keeps the
+// stride-R writes of a pass at two wavefronts per warp.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int line_stride(int N) { return N + N / 16 + 1; }
+__device__ __forceinline__ int lidx(int LS, int l, int pos) { return l * LS + pos + (pos >> 4); }
+
+template <typename C, int N, int NT, int E, int DIR, bool EXACT, int R, int NS>
+__device__ __forceinline__ void regs_pass_line(C (&v)[E], const C* __restrict__ tw) {
+  constexpr int I = E / R;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < I; ++i) {
+    const int j = (tid + i * NT) % (N / R);
+    if constexpr (NS > 1) {
+      const int k = j % NS;
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[i * R + r] = twiddle_mul<DIR, EXACT, true, N>(v[i * R + r], tw, (k * r) * (N / (NS * R)));
+    }
+    dft<R, DIR>(&v[i * R]);
+  }
+}
+
+template <typename C, int N, int NT, int E, int R, int NS>
+__device__ __forceinline__ void regs_to_smem_line(const C (&v)[E], C* buf) {
+  constexpr int I = E / R, LS = line_stride(N);
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < I; ++i) {
+    const int w = tid + i * NT, j = w % (N / R), l = w / (N / R);
+    const int base = (j / NS) * NS * R + j % NS;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[lidx(LS, l, base + r * NS)] = v[i * R + r];
+  }
+}
+
+template <typename C, int N, int NT, int E, int R>
+__device__ __forceinline__ void smem_to_regs_line(C (&v)[E], const C* buf) {
+  constexpr int I = E / R, LS = line_stride(N);
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < I; ++i) {
+    const int w = tid + i * NT, j = w % (N / R), l = w / (N / R);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[i * R + r] = buf[lidx(LS, l, j + r * (N / R))];
+  }
+}
+
+// Passes PASS..last on v; on return v holds the outputs of the last pass at
+// positions j + r N/R_last of line l (item mapping of the last radix). The
+// twiddle table tw is in shared memory.
+template <typename C, int N, int NT, int E, int DIR, bool EXACT, int PASS, int NS>
+__device__ __forceinline__ void regs_fft_line(C (&v)[E], C* buf, const C* __restrict__ tw) {
+  constexpr RadixPlan P = radix_plan(N);
+  constexpr int R = P.r[PASS];
+  regs_pass_line<C, N, NT, E, DIR, EXACT, R, NS>(v, tw);
+  if constexpr (PASS + 1 < P.npass) {
+    constexpr int R2 = P.r[PASS + 1];
+    regs_to_smem_line<C, N, NT, E, R, NS>(v, buf);
+    __syncthreads();
+    smem_to_regs_line<C, N, NT, E, R2>(v, buf);
+    __syncthreads();
+    regs_fft_line<C, N, NT, E, DIR, EXACT, PASS + 1, NS * R>(v, buf, tw);
+  }
 }
 
 }  // namespace fse

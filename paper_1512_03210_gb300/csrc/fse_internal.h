@@ -54,7 +54,7 @@ fse_status cuda_fail(fse_plan* p, cudaError_t e, const char* where);
 fse_status launched(fse_plan* P, cudaError_t e, const char* where);
 cudaEvent_t prof_begin(fse_plan* P);
 void prof_end(fse_plan* P, int kind, cudaEvent_t a);
-fse_status col(fse_plan* P, int kind, int N, int mode, int dir, const ColArgs& a, const MulArgs& m);
+fse_status col(fse_plan* P, int kind, int N, int var, const ColArgs& a, const MulArgs& m);
 fse_status xpass(fse_plan* P, int kind, const XArgs& a);
 int tiles(fse_plan* P, int N, int ncols);
 XArgs x_args(fse_plan* P, void* psi, void* spec);

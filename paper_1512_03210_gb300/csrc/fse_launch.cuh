@@ -26,33 +26,33 @@ static cudaError_t allow_smem(F* fn, size_t bytes, std::atomic<unsigned long lon
   return e;
 }
 
-template <typename Real, int N, int MODE, int DIR>
+template <typename Real, int N, int VAR>
 static cudaError_t col_launch(const ColArgs& a, const MulArgs& m, const void* tw, cudaStream_t st) {
-  typedef typename Cplx<Real>::T C;
-  constexpr int NCOL = ncol_for(N, sizeof(C));
-  constexpr int NT = nt_for(N, NCOL);
-  const size_t smem = sizeof(C) * (size_t)N * (NCOL + 1);
+  typedef ColCfg<Real, N> K;
+  typedef typename K::C C;
+  const size_t smem = K::smem_bytes(VAR);
   static std::atomic<unsigned long long> done{0};
-  cudaError_t e = allow_smem(k_colpass<Real, N, MODE, DIR>, smem, done);
+  cudaError_t e = allow_smem(k_colpass<Real, N, VAR>, smem, done);
   if (e != cudaSuccess) return e;
   const int blocks = a.nplanes * a.tiles_per_plane;
   if (blocks <= 0) return cudaSuccess;
-  k_colpass<Real, N, MODE, DIR><<<blocks, NT, smem, st>>>(a, m, reinterpret_cast<const C*>(tw));
+  k_colpass<Real, N, VAR><<<blocks, K::NT, smem, st>>>(a, m, reinterpret_cast<const C*>(tw));
   return cudaGetLastError();
 }
 
 template <typename Real>
-cudaError_t launch_colpass(int N, int mode, int dir, const ColArgs& a, const MulArgs& m,
-                           const void* tw, cudaStream_t st) {
+cudaError_t launch_colpass(int N, int var, const ColArgs& a, const MulArgs& m, const void* tw, cudaStream_t st) {
   switch (N) {
-#define FSE_CASE(n)                                                        \
-  case n:                                                                  \
-    if (mode == 0) {                                                       \
-      return dir < 0 ? col_launch<Real, n, 0, -1>(a, m, tw, st)            \
-                     : col_launch<Real, n, 0, +1>(a, m, tw, st);           \
-    }                                                                      \
-    return mode == 1 ? col_launch<Real, n, 1, -1>(a, m, tw, st)            \
-                     : col_launch<Real, n, 2, -1>(a, m, tw, st);
+#define FSE_CASE(n)                                                         \
+  case n:                                                                   \
+    switch (var) {                                                          \
+      case COL_FWD: return col_launch<Real, n, COL_FWD>(a, m, tw, st);      \
+      case COL_INV: return col_launch<Real, n, COL_INV>(a, m, tw, st);      \
+      case COL_PADF: return col_launch<Real, n, COL_PADF>(a, m, tw, st);    \
+      case COL_CROPI: return col_launch<Real, n, COL_CROPI>(a, m, tw, st);  \
+      case COL_KIN: return col_launch<Real, n, COL_KIN>(a, m, tw, st);      \
+      default: return col_launch<Real, n, COL_KHAT>(a, m, tw, st);          \
+    }
     FSE_COL_SIZES(FSE_CASE)
 #undef FSE_CASE
     default:
@@ -61,7 +61,7 @@ cudaError_t launch_colpass(int N, int mode, int dir, const ColArgs& a, const Mul
 }
 
 template <typename Real> int colpass_ncol(int N) {
-  return ncol_for(N, 2 * (int)sizeof(Real));
+  return col_ncol(N, 2 * (int)sizeof(Real));
 }
 
 template <typename Real, int NX, int KIND>

@@ -216,12 +216,12 @@ fse_status fft_full(fse_plan* P, void* buf, int dir) {
   ColArgs az{buf, P->nx, (long long)P->nx * P->ny, P->ny, P->nx, P->nz, P->nz, tiles(P, P->nz, P->nx)};
   if (dir < 0) {
     if ((st = xpass(P, XP_FWD, xa)) != FSE_OK) return st;
-    if ((st = col(P, FSE_PASS_OTHER, P->ny, 0, -1, ay, m)) != FSE_OK) return st;
-    if (P->dim == 3 && (st = col(P, FSE_PASS_OTHER, P->nz, 0, -1, az, m)) != FSE_OK) return st;
+    if ((st = col(P, FSE_PASS_OTHER, P->ny, COL_FWD, ay, m)) != FSE_OK) return st;
+    if (P->dim == 3 && (st = col(P, FSE_PASS_OTHER, P->nz, COL_FWD, az, m)) != FSE_OK) return st;
     return FSE_OK;
   }
-  if (P->dim == 3 && (st = col(P, FSE_PASS_OTHER, P->nz, 0, +1, az, m)) != FSE_OK) return st;
-  if ((st = col(P, FSE_PASS_OTHER, P->ny, 0, +1, ay, m)) != FSE_OK) return st;
+  if (P->dim == 3 && (st = col(P, FSE_PASS_OTHER, P->nz, COL_INV, az, m)) != FSE_OK) return st;
+  if ((st = col(P, FSE_PASS_OTHER, P->ny, COL_INV, ay, m)) != FSE_OK) return st;
   return xpass(P, XP_INV, xa);
 }
 

@@ -14,11 +14,10 @@
 
 namespace fse {
 
-// tw[m] = exp(-2 pi i m / L), m = 0..L-1, from float64 sincospi. For float
-// tables the pair (c, s) is chosen among the float neighbours of the float64
-// values as the one with |c + i s| closest to 1: every element of a transform
-// meets the same table entries in every step, so a magnitude error of an
-// entry would otherwise act as a fixed gain and make the norm drift.
+// tw[2m] = exp(-2 pi i m / L), m = 0..L-1, from float64 sincospi, and
+// tw[2m+1] the rounded remainder (exact minus tw[2m]). For float tables the
+// pair (c, s) is chosen among the float neighbours of the float64 values as
+// the one with |c + i s| closest to 1.
 __device__ __forceinline__ void round_pair(double c, double s, float2* out) {
   const float c0 = (float)c, s0 = (float)s;
   const float cc[2] = {c0, (double)c0 > c ? nextafterf(c0, -2.f) : nextafterf(c0, 2.f)};
@@ -43,7 +42,9 @@ __global__ void k_twiddles(typename Cplx<Real>::T* tw, int L) {
   if (m >= L) return;
   double s, c;
   sincospi(-2.0 * (double)m / (double)L, &s, &c);
-  round_pair(c, s, &tw[m]);
+  round_pair(c, s, &tw[2 * m]);
+  // rounded remainder of the exact twiddle (second term of the exact products)
+  tw[2 * m + 1] = mk(Real(c - (double)tw[2 * m].x), Real(s - (double)tw[2 * m].y));
 }
 
 // Kinetic multipliers exp(-i theta_k) (half step, theta = dt/4 (|k|^2+m^2)^s)
