@@ -269,14 +269,22 @@ fse_status kinetic_yz(fse_plan* P, void* psi, double f, double dt) {
     return fail(P, FSE_ERR_INVALID, "kinetic factor must be 1, 2 or -1");
   }
   m.conj = f < 0.0;
+  m.lx = P->nx;
   fse_status st;
   if (P->dim == 2) {
+    m.lp = 0;
+    m.lr = P->ny;
+    m.kin_sr = P->nx / 2 + 1;
     m.scale = 1.0 / ((double)P->nx * P->ny);
     ColArgs a{psi, 0, P->nx, 1, P->nx, P->ny, P->ny, tiles(P, P->ny, P->nx)};
     return col(P, FSE_PASS_KIN, P->ny, COL_KIN, a, m);
   }
   ColArgs ay{psi, (long long)P->nx * P->ny, P->nx, P->nz, P->nx, P->ny, P->ny, tiles(P, P->ny, P->nx)};
   if ((st = col(P, FSE_PASS_COL, P->ny, COL_FWD, ay, m)) != FSE_OK) return st;
+  m.lp = P->ny;
+  m.lr = P->nz;
+  m.kin_sp = P->nx / 2 + 1;
+  m.kin_sr = (long long)(P->nx / 2 + 1) * (P->ny / 2 + 1);
   m.scale = 1.0 / ((double)P->nx * P->ny * P->nz);
   ColArgs az{psi, P->nx, (long long)P->nx * P->ny, P->ny, P->nx, P->nz, P->nz, tiles(P, P->nz, P->nx)};
   if ((st = col(P, FSE_PASS_KIN, P->nz, COL_KIN, az, m)) != FSE_OK) return st;
@@ -493,11 +501,11 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
   P->off_chat = off;
   const size_t nchat = (size_t)(P->nx + 1) * (P->ny + 1) * (p.dim == 3 ? P->nz + 1 : 1);
   off = align256(off + nchat * P->rsize);
-  const size_t psi_elems = (size_t)P->nx * P->ny * P->nz;
+  const size_t kin_elems = (size_t)(P->nx / 2 + 1) * (P->ny / 2 + 1) * (p.dim == 3 ? P->nz / 2 + 1 : 1);
   P->off_kin_half = off;
-  off = align256(off + psi_elems * P->csize);
+  off = align256(off + kin_elems * P->csize);
   P->off_kin_full = off;
-  off = align256(off + psi_elems * P->csize);
+  off = align256(off + kin_elems * P->csize);
   P->off_spec = off;
   const size_t spec_rows = (size_t)(p.dim == 3 ? P->nz * 2 * P->ny : P->ny);
   const size_t spec_bytes = spec_rows * P->sx * P->csize;

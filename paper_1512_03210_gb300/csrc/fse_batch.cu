@@ -214,14 +214,14 @@ fse_status fse_batch_create(const fse_params* runs, int nruns, void* stream, fse
     off = al(off + nb);
     G.off_desc = off;
     off = al(off + sizeof(BatchRun) * G.runs.size());
-    const size_t psi_bytes = (size_t)G.nx * G.ny * 8;
+    const size_t kin_bytes = (size_t)(G.nx / 2 + 1) * (G.ny / 2 + 1) * 8;
     const size_t spec_bytes = (size_t)G.ny * G.plan->sx * 8;
     for (size_t k = 1; k < G.runs.size(); ++k) {
       const int r = G.runs[k];
       B->off_kh[r] = off;
-      off = al(off + psi_bytes);
+      off = al(off + kin_bytes);
       B->off_kf[r] = off;
-      off = al(off + psi_bytes);
+      off = al(off + kin_bytes);
       B->off_spec[r] = off;
       off = al(off + spec_bytes);
     }
@@ -307,6 +307,9 @@ fse_status fse_batch_step(fse_batch_t B, void* const* psi, double t0, int nsteps
     MulArgs mk1;
     std::memset(&mk1, 0, sizeof(mk1));
     mk1.mode = MUL_KIN;
+    mk1.lx = P->nx;
+    mk1.lr = P->ny;
+    mk1.kin_sr = P->nx / 2 + 1;
     mk1.scale = 1.0 / ((double)P->nx * P->ny);
     ColArgs ck{nullptr, 0, P->nx, 1, P->nx, P->ny, P->ny, tiles(P, P->ny, P->nx)};
     MulArgs mk2;

@@ -197,14 +197,11 @@ __device__ __forceinline__ float norm_err(float c, float s) {
 }
 
 // v times twiddle m of the table (conjugated for the inverse transform).
-// SM: the table sits in shared memory, split into the rounded pairs tw[0..N)
-// followed by the remainders tw[N..2N) (plain loads, consecutive entries on
-// consecutive banks); otherwise it is the interleaved global table.
-template <int DIR, bool EXACT, bool SM = false, int NTW = 0, typename C>
+template <int DIR, bool EXACT, typename C>
 __device__ __forceinline__ C twiddle_mul(C v, const C* __restrict__ tw, int m) {
-  const C w = SM ? tw[m] : __ldg(&tw[2 * m]);
+  const C w = __ldg(&tw[2 * m]);
   if constexpr (EXACT && sizeof(C) == 8) {
-    const C l = SM ? tw[NTW + m] : __ldg(&tw[2 * m + 1]);
+    const C l = __ldg(&tw[2 * m + 1]);
     if constexpr (DIR < 0) {
       const float lr = v.x * l.x - v.y * l.y, li = v.x * l.y + v.y * l.x;
       return mk(fmaf(v.x, w.x, fmaf(-v.y, w.y, lr)), fmaf(v.x, w.y, fmaf(v.y, w.x, li)));
@@ -371,76 +368,6 @@ __device__ __forceinline__ void regs_fft(C (&v)[E], C* buf, const C* __restrict_
     smem_to_regs<C, N, NCOL, NT, E, R2>(v, buf);
     __syncthreads();
     regs_fft<C, N, NCOL, NT, E, DIR, EXACT, PASS + 1, NS * R>(v, buf, tw);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Register-staged Stockham for contiguous lines (the x axis). Item w of a
-// pass of radix R maps to (line l, butterfly j) with j fastest: j = w % (N/R),
-// l = w / (N/R), so the first pass's loads and the last pass's stores touch
-// consecutive addresses. Shared memory holds the NL lines of a tile line by
-// line with one padding slot every 16 elements (lidx), which keeps the
-// stride-R writes of a pass at two wavefronts per warp.
-// ---------------------------------------------------------------------------
-__host__ __device__ constexpr int line_stride(int N) { return N + N / 16 + 1; }
-__device__ __forceinline__ int lidx(int LS, int l, int pos) { return l * LS + pos + (pos >> 4); }
-
-template <typename C, int N, int NT, int E, int DIR, bool EXACT, int R, int NS>
-__device__ __forceinline__ void regs_pass_line(C (&v)[E], const C* __restrict__ tw) {
-  constexpr int I = E / R;
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int i = 0; i < I; ++i) {
-    const int j = (tid + i * NT) % (N / R);
-    if constexpr (NS > 1) {
-      const int k = j % NS;
-#pragma unroll
-      for (int r = 1; r < R; ++r) v[i * R + r] = twiddle_mul<DIR, EXACT, true, N>(v[i * R + r], tw, (k * r) * (N / (NS * R)));
-    }
-    dft<R, DIR>(&v[i * R]);
-  }
-}
-
-template <typename C, int N, int NT, int E, int R, int NS>
-__device__ __forceinline__ void regs_to_smem_line(const C (&v)[E], C* buf) {
-  constexpr int I = E / R, LS = line_stride(N);
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int i = 0; i < I; ++i) {
-    const int w = tid + i * NT, j = w % (N / R), l = w / (N / R);
-    const int base = (j / NS) * NS * R + j % NS;
-#pragma unroll
-    for (int r = 0; r < R; ++r) buf[lidx(LS, l, base + r * NS)] = v[i * R + r];
-  }
-}
-
-template <typename C, int N, int NT, int E, int R>
-__device__ __forceinline__ void smem_to_regs_line(C (&v)[E], const C* buf) {
-  constexpr int I = E / R, LS = line_stride(N);
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int i = 0; i < I; ++i) {
-    const int w = tid + i * NT, j = w % (N / R), l = w / (N / R);
-#pragma unroll
-    for (int r = 0; r < R; ++r) v[i * R + r] = buf[lidx(LS, l, j + r * (N / R))];
-  }
-}
-
-// Passes PASS..last on v; on return v holds the outputs of the last pass at
-// positions j + r N/R_last of line l (item mapping of the last radix). The
-// twiddle table tw is in shared memory.
-template <typename C, int N, int NT, int E, int DIR, bool EXACT, int PASS, int NS>
-__device__ __forceinline__ void regs_fft_line(C (&v)[E], C* buf, const C* __restrict__ tw) {
-  constexpr RadixPlan P = radix_plan(N);
-  constexpr int R = P.r[PASS];
-  regs_pass_line<C, N, NT, E, DIR, EXACT, R, NS>(v, tw);
-  if constexpr (PASS + 1 < P.npass) {
-    constexpr int R2 = P.r[PASS + 1];
-    regs_to_smem_line<C, N, NT, E, R, NS>(v, buf);
-    __syncthreads();
-    smem_to_regs_line<C, N, NT, E, R2>(v, buf);
-    __syncthreads();
-    regs_fft_line<C, N, NT, E, DIR, EXACT, PASS + 1, NS * R>(v, buf, tw);
   }
 }
 

@@ -64,7 +64,8 @@ struct MulArgs {
   double q[6];       // DDI: 3*scale*(Mxx, Myy, Mrr..): see host code (x, plane, row)
   const void* chat;
   long long chat_sp, chat_sr;
-  const void* kin;   // kinetic: table of exp(-i f theta_k) in the field's layout
+  const void* kin;   // kinetic: octant table of exp(-i f theta_k) on |p_j| = 0..n_j/2
+  long long kin_sp, kin_sr;  // kinetic: octant strides of the plane and row axes
   int conj;          // kinetic: multiply by the conjugate of the table (adjoint)
 };
 
@@ -188,16 +189,18 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
     regs_fft<C, N, NCOL, NT, E, -1, EXACT, 0, 1>(v, buf, tw);
     // spectral multiplier on the outputs (row = frequency index along the axis)
     if constexpr (VAR == COL_KIN) {
-      const C* tab = reinterpret_cast<const C*>(m.kin) + (long long)plane * a.plane_stride + c0;
+      // kinetic phase exp(-i f theta_k) from the plan's octant table, indexed by
+      // |p_x| (column), |p_plane| and |p_row| (row = frequency index along the axis)
+      const C* tab = reinterpret_cast<const C*>(m.kin) + (m.lp ? (long long)abs(wrap_index(plane, m.lp)) * m.kin_sp : 0);
       const Real sc = Real(m.scale);
 #pragma unroll
       for (int i = 0; i < E / RL; ++i) {
         const int w = tid + i * NT, c = w % NCOL, j = w / NCOL;
+        const int ax = abs(wrap_index(min(c0 + c, m.lx - 1), m.lx));
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
           const int row = j + r * (N / RL);
-          // kinetic phase exp(-i f theta_k) from the plan's table (same layout as the field)
-          const C t = c < ncv ? __ldg(&tab[(long long)row * a.line_stride + c]) : mk(Real(1), Real(0));
+          const C t = c < ncv ? __ldg(&tab[(long long)abs(wrap_index(row, m.lr)) * m.kin_sr + ax]) : mk(Real(1), Real(0));
           C x = unit_mul(v[i * RL + r], t.x, t.y, m.conj != 0);
           buf[row * LDS + c] = mk(sc * x.x, sc * x.y);
         }
@@ -263,47 +266,104 @@ k_colpass(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__ tw) {
 }
 
 // ---------------------------------------------------------------------------
-// x passes over tiles of NL consecutive lines (rows of psi), register-staged:
-// the transforms of length NX (wave function) and 2 NX (zero-padded density,
-// two real lines packed as the real and imaginary part of one complex line)
-// read their first-pass inputs from global memory and keep their last-pass
-// outputs in registers; shared memory only carries the exchanges between
-// passes (line layout with padding, see lidx).
+// x passes over tiles of NCOL consecutive lines (rows of psi). A tile is
+// transposed into shared memory (column layout, LDS = NCOL + 1) so that one
+// Stockham routine serves every axis; the real density is handled as two
+// lines packed into one complex line.
 // ---------------------------------------------------------------------------
-__host__ __device__ constexpr int lcm2(int a, int b) {
-  int x = a, y = b;
-  while (y) {
-    const int t = x % y;
-    x = y;
-    y = t;
-  }
-  return a / x * b;
-}
-
 template <typename Real, int NX>
 struct XCfg {
   typedef typename Cplx<Real>::T C;
-  static constexpr int N2 = 2 * NX;
-  static constexpr int E = lcm2(plan_lcm(NX), plan_lcm(N2));   // elements per thread
-  static constexpr int TT = sizeof(Real) == 4 ? 512 : 256;      // target threads per tile
-  static constexpr int NL0 = TT * E / NX;
-  static constexpr int NL = NL0 < 2 ? 2 : (NL0 > 64 ? 64 : NL0);  // lines per tile (even)
-  static constexpr int NCOL = NL;
-  static constexpr int NT = NL * NX / E;
-  static constexpr int LS = line_stride(NX), LS2 = line_stride(N2);
-  static constexpr int R0 = radix_plan(NX).r[0], RL = radix_plan(NX).r[radix_plan(NX).npass - 1];
-  static constexpr int Q0 = radix_plan(N2).r[0], QL = radix_plan(N2).r[radix_plan(N2).npass - 1];
-  static constexpr int XBUF = NL * LS > (NL / 2) * LS2 ? NL * LS : (NL / 2) * LS2;
-  static constexpr size_t smem_elems() { return (size_t)XBUF; }
-  // exchange buffer, then the twiddle tables of lengths NX and 2 NX (two entries per twiddle)
-  static constexpr size_t smem_bytes() { return sizeof(C) * (smem_elems() + 2 * NX + 2 * N2); }
-  // register budget: 64 per thread for 8 float elements, 128 for more (and for double)
-  static constexpr int RB = (sizeof(Real) == 4 && E <= 8) ? 1024 : 512;
-  static constexpr int MINB = RB / NT > 0 ? RB / NT : 1;
+  static constexpr int NCOL = ncol_for(2 * NX, sizeof(C)) < 2 ? 2 : ncol_for(2 * NX, sizeof(C));
+  static constexpr int NT = 256;
+  static constexpr int LDS = NCOL + 1;
+  static constexpr int LDS2 = NCOL / 2 + 1;
+  static constexpr int TOT = NCOL * NX;
+  static constexpr int PER = (TOT + NT - 1) / NT;
+  static constexpr size_t smem_bytes() {
+    return sizeof(C) * (size_t)((NX * LDS) > (2 * NX * LDS2) ? (NX * LDS) : (2 * NX * LDS2));
+  }
+  static constexpr int MINB = sizeof(Real) == 4 ? 4 : 2;
 };
 
 __device__ __forceinline__ long long srow(int l, int ny, int mul) {
   return (long long)(l / ny) * (mul * ny) + (l % ny);
+}
+
+// Real values of the NCOL lines of a tile (one per (line, x) item of the
+// thread, PER items) -> x-half-spectra of the zero-padded lines in S. Two real
+// lines form one complex line; one FFT of length 2 NX; the two spectra are
+// separated with A_k = (Z_k + conj Z_-k)/2, B_k = (Z_k - conj Z_-k)/(2i).
+// The caller has synchronised (buf free); ends without a barrier.
+template <typename Real, int NX>
+__device__ __forceinline__ void r2c_rows(const XArgs& a, typename Cplx<Real>::T* buf, int l0,
+                                         const typename Cplx<Real>::T* __restrict__ tw2n,
+                                         const Real (&val)[XCfg<Real, NX>::PER]) {
+  typedef XCfg<Real, NX> K;
+  typedef typename K::C C;
+  constexpr int NCOL = K::NCOL, NT = K::NT, LDS2 = K::LDS2, TOT = K::TOT, PER = K::PER;
+  const int tid = threadIdx.x;
+  C* S = reinterpret_cast<C*>(a.spec);
+#pragma unroll
+  for (int it = 0; it < PER; ++it) {
+    const int idx = tid + it * NT;
+    if ((TOT % NT) == 0 || idx < TOT) {
+      const int l = idx / NX, x = idx % NX;
+      reinterpret_cast<Real*>(&buf[x * LDS2 + (l >> 1)])[l & 1] = val[it];
+    }
+  }
+  for (int idx = tid; idx < (NCOL / 2) * NX; idx += NT) {
+    const int q = idx / NX, x = NX + idx % NX;
+    buf[x * LDS2 + q] = mk(Real(0), Real(0));
+  }
+  __syncthreads();
+  fft_tile<C, 2 * NX, NCOL / 2, NT, -1, false>(buf, tw2n);
+  for (int idx = tid; idx < (NCOL / 2) * (NX + 1); idx += NT) {
+    const int q = idx / (NX + 1), k = idx % (NX + 1);
+    const C zk = buf[k * LDS2 + q];
+    const C zm = buf[((2 * NX - k) % (2 * NX)) * LDS2 + q];
+    const int la = l0 + 2 * q;
+    const C A = mk(Real(0.5) * (zk.x + zm.x), Real(0.5) * (zk.y - zm.y));
+    const C B = mk(Real(0.5) * (zk.y + zm.y), Real(0.5) * (zm.x - zk.x));
+    if (la < a.nlines) S[srow(la, a.ny, a.srow_mul) * a.sx + k] = A;
+    if (la + 1 < a.nlines) S[srow(la + 1, a.ny, a.srow_mul) * a.sx + k] = B;
+  }
+}
+
+// x-half-spectra in S of the tile's lines -> real values (cropped C2R of length
+// 2 NX, two lines per complex line via the Hermitian extension Z = A + i B).
+// The caller has synchronised (buf free); ends after the values are read
+// (the caller synchronises before reusing buf).
+template <typename Real, int NX>
+__device__ __forceinline__ void c2r_rows(const XArgs& a, typename Cplx<Real>::T* buf, int l0,
+                                         const typename Cplx<Real>::T* __restrict__ tw2n,
+                                         Real (&val)[XCfg<Real, NX>::PER]) {
+  typedef XCfg<Real, NX> K;
+  typedef typename K::C C;
+  constexpr int NCOL = K::NCOL, NT = K::NT, LDS2 = K::LDS2, TOT = K::TOT, PER = K::PER;
+  const int tid = threadIdx.x;
+  const C* S = reinterpret_cast<const C*>(a.spec);
+  for (int idx = tid; idx < (NCOL / 2) * (NX + 1); idx += NT) {
+    const int q = idx / (NX + 1), k = idx % (NX + 1);
+    const int la = l0 + 2 * q;
+    C A = mk(Real(0), Real(0)), B = A;
+    if (la < a.nlines) A = S[srow(la, a.ny, a.srow_mul) * a.sx + k];
+    if (la + 1 < a.nlines) B = S[srow(la + 1, a.ny, a.srow_mul) * a.sx + k];
+    buf[k * LDS2 + q] = mk(A.x - B.y, A.y + B.x);
+    if (k > 0 && k < NX) buf[(2 * NX - k) * LDS2 + q] = mk(A.x + B.y, B.x - A.y);
+  }
+  __syncthreads();
+  fft_tile<C, 2 * NX, NCOL / 2, NT, +1, false>(buf, tw2n);
+#pragma unroll
+  for (int it = 0; it < PER; ++it) {
+    const int idx = tid + it * NT;
+    val[it] = Real(0);
+    if ((TOT % NT) == 0 || idx < TOT) {
+      const int l = idx / NX, x = idx % NX;
+      const C z = buf[x * LDS2 + (l >> 1)];
+      val[it] = (l & 1) ? z.y : z.x;
+    }
+  }
 }
 
 template <typename Real>
@@ -314,219 +374,166 @@ __device__ __forceinline__ Real trap_phase(const XArgs& a, int x, int lg) {
   return Real(a.pa) * X * X + Real(a.pb) * Y * Y + Real(a.pc) * X * Y + Real(a.pe) * Z * Z;
 }
 
-// Packed inverse transform of length 2 NX of the x-half-spectra in S of the
-// line pairs (2q, 2q+1) of the tile (C2R of two lines at once via
-// Z = A + i B with the Hermitian extension, read straight from S). On return
-// z holds Z at positions j + r 2NX/QL of pair q (item mapping of the last radix).
-template <typename Real, int NX>
-__device__ __forceinline__ void c2r_pairs(const XArgs& a, typename Cplx<Real>::T* buf, int l0,
-                                          const typename Cplx<Real>::T* __restrict__ tw2n,
-                                          typename Cplx<Real>::T (&z)[XCfg<Real, NX>::E]) {
-  typedef XCfg<Real, NX> K;
-  typedef typename K::C C;
-  constexpr int N2 = K::N2, NT = K::NT, E = K::E, Q0 = K::Q0;
-  const int tid = threadIdx.x;
-  const C* S = reinterpret_cast<const C*>(a.spec);
-#pragma unroll
-  for (int i = 0; i < E / Q0; ++i) {
-    const int w = tid + i * NT, j = w % (N2 / Q0), q = w / (N2 / Q0);
-    const int la = l0 + 2 * q;
-    const C* ra = S + srow(la, a.ny, a.srow_mul) * a.sx;
-    const C* rb = S + srow(la + 1, a.ny, a.srow_mul) * a.sx;
-    const bool va = la < a.nlines, vb = la + 1 < a.nlines;
-#pragma unroll
-    for (int r = 0; r < Q0; ++r) {
-      const int pos = j + r * (N2 / Q0);
-      const bool lo = pos <= NX;
-      const int k = lo ? pos : N2 - pos;
-      C A = va ? ra[k] : mk(Real(0), Real(0));
-      C B = vb ? rb[k] : mk(Real(0), Real(0));
-      if (!lo) {
-        A.y = -A.y;
-        B.y = -B.y;
-      }
-      z[i * Q0 + r] = mk(A.x - B.y, A.y + B.x);
-    }
-  }
-  regs_fft_line<C, N2, NT, E, +1, false, 0, 1>(z, buf, tw2n);
-}
-
-// Real values val of the tile's lines, held as pairs (line 2q in .x, line 2q+1
-// in .y) at positions pos < NX of pair q in the item mapping of the packed
-// transform's last radix (or written to buf by the caller), -> x-half-spectra
-// of the zero-padded lines in S. The caller has placed the packed values in
-// buf (positions < NX) and synchronised.
-template <typename Real, int NX>
-__device__ __forceinline__ void r2c_pairs_from_smem(const XArgs& a, typename Cplx<Real>::T* buf, int l0,
-                                                    const typename Cplx<Real>::T* __restrict__ tw2n) {
-  typedef XCfg<Real, NX> K;
-  typedef typename K::C C;
-  constexpr int N2 = K::N2, NT = K::NT, E = K::E, Q0 = K::Q0, QL = K::QL, LS2 = K::LS2, NL = K::NL;
-  constexpr bool HALF_IN = (Q0 % 2 == 0);
-  const int tid = threadIdx.x;
-  C z[E];
-#pragma unroll
-  for (int i = 0; i < E / Q0; ++i) {
-    const int w = tid + i * NT, j = w % (N2 / Q0), q = w / (N2 / Q0);
-#pragma unroll
-    for (int r = 0; r < Q0; ++r) {
-      const int pos = j + r * (N2 / Q0);
-      if (HALF_IN && r >= Q0 / 2) {
-        z[i * Q0 + r] = mk(Real(0), Real(0));
-      } else {
-        z[i * Q0 + r] = pos < NX ? buf[lidx(LS2, q, pos)] : mk(Real(0), Real(0));
-      }
-    }
-  }
-  __syncthreads();
-  regs_fft_line<C, N2, NT, E, -1, false, 0, 1>(z, buf, tw2n);
-  // separation A_k = (Z_k + conj Z_-k)/2, B_k = (Z_k - conj Z_-k)/(2i) needs Z at k and 2NX - k
-#pragma unroll
-  for (int i = 0; i < E / QL; ++i) {
-    const int w = tid + i * NT, j = w % (N2 / QL), q = w / (N2 / QL);
-#pragma unroll
-    for (int r = 0; r < QL; ++r) buf[lidx(LS2, q, j + r * (N2 / QL))] = z[i * QL + r];
-  }
-  __syncthreads();
-  C* S = reinterpret_cast<C*>(a.spec);
-  for (int idx = tid; idx < (NL / 2) * (NX + 1); idx += NT) {
-    const int q = idx / (NX + 1), k = idx % (NX + 1);
-    const C zk = buf[lidx(LS2, q, k)];
-    const C zm = buf[lidx(LS2, q, (N2 - k) % N2)];
-    const int la = l0 + 2 * q;
-    const C A = mk(Real(0.5) * (zk.x + zm.x), Real(0.5) * (zk.y - zm.y));
-    const C B = mk(Real(0.5) * (zk.y + zm.y), Real(0.5) * (zm.x - zk.x));
-    if (la < a.nlines) S[srow(la, a.ny, a.srow_mul) * a.sx + k] = A;
-    if (la + 1 < a.nlines) S[srow(la + 1, a.ny, a.srow_mul) * a.sx + k] = B;
-  }
-}
-
 template <typename Real, int NX, int KIND>
-__device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<Real>::T* __restrict__ twn_g,
-                                           const typename Cplx<Real>::T* __restrict__ tw2n_g, int bid) {
+__device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<Real>::T* __restrict__ twn,
+                                           const typename Cplx<Real>::T* __restrict__ tw2n, int bid) {
   typedef XCfg<Real, NX> K;
   typedef typename K::C C;
-  constexpr int N2 = K::N2, NL = K::NL, NT = K::NT, E = K::E, LS = K::LS, LS2 = K::LS2;
-  constexpr int R0 = K::R0, RL = K::RL, QL = K::QL;
+  constexpr int NCOL = K::NCOL, NT = K::NT, LDS = K::LDS, TOT = K::TOT, PER = K::PER;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double red[32];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int tid = threadIdx.x;
-  const int l0 = bid * NL;
+  const int l0 = bid * NCOL;
   C* psi = reinterpret_cast<C*>(a.psi);
-  C v[E];
-  // twiddle tables into shared memory: every lane of a warp needs a different entry
-  C* twn = buf + K::XBUF;
-  C* tw2n = twn + 2 * NX;
-  for (int i = tid; i < 2 * NX; i += NT) twn[(i & 1) * NX + (i >> 1)] = __ldg(&twn_g[i]);
-  for (int i = tid; i < 2 * N2; i += NT) tw2n[(i & 1) * N2 + (i >> 1)] = __ldg(&tw2n_g[i]);
-  __syncthreads();
 
   if constexpr (KIND == XP_FWD || KIND == XP_INV || KIND == XP_E) {
-#pragma unroll
-    for (int i = 0; i < E / R0; ++i) {
-      const int w = tid + i * NT, j = w % (NX / R0), l = w / (NX / R0);
-      const bool ok = l0 + l < a.nlines;
-#pragma unroll
-      for (int r = 0; r < R0; ++r)
-        v[i * R0 + r] = ok ? psi[(long long)(l0 + l) * NX + j + r * (NX / R0)] : mk(Real(0), Real(0));
+#pragma unroll 8
+    for (int it = 0; it < PER; ++it) {
+      const int idx = tid + it * NT;
+      if ((TOT % NT) == 0 || idx < TOT) {
+        const int l = idx / NX, x = idx % NX;
+        C v = mk(Real(0), Real(0));
+        if (l0 + l < a.nlines) v = psi[(long long)(l0 + l) * NX + x];
+        buf[x * LDS + l] = v;
+      }
     }
-    regs_fft_line<C, NX, NT, E, (KIND == XP_FWD ? -1 : +1), true, 0, 1>(v, buf, twn);
-    Real rho[E];
+    __syncthreads();
+    fft_tile<C, NX, NCOL, NT, (KIND == XP_FWD ? -1 : +1), true>(buf, twn);
+    Real rho[PER];
 #pragma unroll
-    for (int i = 0; i < E / RL; ++i) {
-      const int w = tid + i * NT, j = w % (NX / RL), l = w / (NX / RL);
-      const bool ok = l0 + l < a.nlines;
-#pragma unroll
-      for (int r = 0; r < RL; ++r) {
-        const int pos = j + r * (NX / RL);
-        const C u = v[i * RL + r];
-        if (ok) psi[(long long)(l0 + l) * NX + pos] = u;
-        rho[i * RL + r] = u.x * u.x + u.y * u.y;
+    for (int it = 0; it < PER; ++it) {
+      const int idx = tid + it * NT;
+      rho[it] = Real(0);
+      if ((TOT % NT) == 0 || idx < TOT) {
+        const int l = idx / NX, x = idx % NX;
+        const C v = buf[x * LDS + l];
+        if (l0 + l < a.nlines) psi[(long long)(l0 + l) * NX + x] = v;
+        rho[it] = v.x * v.x + v.y * v.y;
       }
     }
     if constexpr (KIND == XP_E || KIND == XP_INV) {
       if (a.part) {  // float64 mass partial of this tile (renormalisation)
         double acc = 0.0;
 #pragma unroll
-        for (int e = 0; e < E; ++e) acc += (double)rho[e];
+        for (int it = 0; it < PER; ++it) acc += (double)rho[it];
         acc = block_sum(acc, red);
         if (tid == 0) a.part[bid] = acc;
       }
     }
     if constexpr (KIND == XP_E) {
-      // densities of lines 2q, 2q+1 as the real and imaginary part of pair q
-#pragma unroll
-      for (int i = 0; i < E / RL; ++i) {
-        const int w = tid + i * NT, j = w % (NX / RL), l = w / (NX / RL);
-#pragma unroll
-        for (int r = 0; r < RL; ++r)
-          reinterpret_cast<Real*>(&buf[lidx(LS2, l >> 1, j + r * (NX / RL))])[l & 1] = rho[i * RL + r];
-      }
       __syncthreads();
-      r2c_pairs_from_smem<Real, NX>(a, buf, l0, tw2n);
+      r2c_rows<Real, NX>(a, buf, l0, tw2n, rho);
     }
-  } else if constexpr (KIND == XP_A || KIND == XP_R) {
+  } else if constexpr (KIND == XP_ADJ1) {
+    // adjoint, first half: g_u2 (in psi) -> h = exp(+i Theta) g_u2 (stored in psi),
+    // r = Im(conj(g_u2) u2) -> x-half-spectra of r in S, trap-gradient partials
+    const C* u1p = reinterpret_cast<const C*>(a.aux);
+    Real vphi[PER];
+#pragma unroll
+    for (int it = 0; it < PER; ++it) vphi[it] = Real(0);
     if (a.use_spec) {
-      C z[E];
-      c2r_pairs<Real, NX>(a, buf, l0, tw2n, z);
-      // outputs at positions < NX carry varphi of both lines of the pair
+      c2r_rows<Real, NX>(a, buf, l0, tw2n, vphi);
+      __syncthreads();
+    }
+    Real rr[PER];
+    double dg0 = 0.0, dg1 = 0.0, dg2 = 0.0;
+#pragma unroll
+    for (int it = 0; it < PER; ++it) {
+      const int idx = tid + it * NT;
+      rr[it] = Real(0);
+      if ((TOT % NT) == 0 || idx < TOT) {
+        const int l = idx / NX, x = idx % NX;
+        const int lg = l0 + l;
+        if (lg < a.nlines) {
+          const long long o = (long long)lg * NX + x;
+          const C u = u1p[o];
+          const C g = psi[o];
+          const Real th = Real(a.beta_dt) * (u.x * u.x + u.y * u.y) + Real(a.lam) * vphi[it] + trap_phase<Real>(a, x, lg);
+          Real sn, cs;
+          sincos(th, &sn, &cs);
+          const C u2 = mk(u.x * cs + u.y * sn, u.y * cs - u.x * sn);
+          const Real r = g.x * u2.y - g.y * u2.x;
+          rr[it] = r;
+          psi[o] = mk(g.x * cs - g.y * sn, g.y * cs + g.x * sn);
+          const double X = a.lo0 + a.h0 * x, Y = a.lo1 + a.h1 * (lg % a.ny), Z = a.lo2 + a.h2 * (lg / a.ny);
+          dg0 += (double)r * (a.dp[0] * X * X + a.dp[1] * Y * Y + a.dp[2] * X * Y + a.dp[3] * Z * Z);
+          dg1 += (double)r * (a.dp[4] * X * X + a.dp[5] * Y * Y + a.dp[6] * X * Y + a.dp[7] * Z * Z);
+          dg2 += (double)r * (a.dp[8] * X * X + a.dp[9] * Y * Y + a.dp[10] * X * Y + a.dp[11] * Z * Z);
+        }
+      }
+    }
+    if (a.part) {
+      dg0 = block_sum(dg0, red);
+      if (tid == 0) a.part[bid] = dg0;
+      dg1 = block_sum(dg1, red);
+      if (tid == 0) a.part[a.part_stride + bid] = dg1;
+      dg2 = block_sum(dg2, red);
+      if (tid == 0) a.part[2 * a.part_stride + bid] = dg2;
+    }
+    if (a.use_spec) {
+      __syncthreads();
+      r2c_rows<Real, NX>(a, buf, l0, tw2n, rr);
+    }
+  } else if constexpr (KIND == XP_ADJ2) {
+    // adjoint, second half: g_u1 = h + 2 q u1, q = dt beta r + lambda Kc r, r = Im(conj(h) u1)
+    const C* u1p = reinterpret_cast<const C*>(a.aux);
+    Real kr[PER];
+#pragma unroll
+    for (int it = 0; it < PER; ++it) kr[it] = Real(0);
+    if (a.use_spec) c2r_rows<Real, NX>(a, buf, l0, tw2n, kr);
+#pragma unroll
+    for (int it = 0; it < PER; ++it) {
+      const int idx = tid + it * NT;
+      if ((TOT % NT) == 0 || idx < TOT) {
+        const int l = idx / NX, x = idx % NX;
+        const int lg = l0 + l;
+        if (lg < a.nlines) {
+          const long long o = (long long)lg * NX + x;
+          const C u = u1p[o];
+          const C h = psi[o];
+          const Real r = h.x * u.y - h.y * u.x;
+          const Real q2 = Real(2) * (Real(a.beta_dt) * r + Real(a.lam) * kr[it]);
+          psi[o] = mk(h.x + q2 * u.x, h.y + q2 * u.y);
+        }
+      }
+    }
+  } else {
+    // XP_A / XP_R: varphi from the cropped C2R of S
+    Real vphi[PER];
+#pragma unroll
+    for (int it = 0; it < PER; ++it) vphi[it] = Real(0);
+    if (a.use_spec) c2r_rows<Real, NX>(a, buf, l0, tw2n, vphi);
+    if constexpr (KIND == XP_R) {
+      // sum over the tile of varphi * |psi|^2 (nonlocal interaction energy density)
       double acc = 0.0;
 #pragma unroll
-      for (int i = 0; i < E / QL; ++i) {
-        const int w = tid + i * NT, j = w % (N2 / QL), q = w / (N2 / QL);
-#pragma unroll
-        for (int r = 0; r < QL; ++r) {
-          const int pos = j + r * (N2 / QL);
-          if ((QL % 2 == 0 && r >= QL / 2) || pos >= NX) continue;
-          const C zz = z[i * QL + r];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int l = 2 * q + h, lg = l0 + l;
-            const Real vphi = h ? zz.y : zz.x;
-            C u2 = mk(Real(0), Real(0));
-            if (lg < a.nlines) {
-              const C u = psi[(long long)lg * NX + pos];
-              const Real rho = u.x * u.x + u.y * u.y;
-              if constexpr (KIND == XP_R) {
-                acc += (double)vphi * (double)rho;
-              } else {
-                const Real th = Real(a.beta_dt) * rho + Real(a.lam) * vphi + trap_phase<Real>(a, pos, lg);
-                Real sn, cs;
-                sincos(th, &sn, &cs);
-                u2 = unit_mul(u, cs, -sn, false);
-                if (a.scale) {
-                  const Real f = Real(*a.scale);
-                  u2 = mk(f * u2.x, f * u2.y);
-                }
-              }
-            }
-            if constexpr (KIND == XP_A) buf[lidx(LS, l, pos)] = u2;
+      for (int it = 0; it < PER; ++it) {
+        const int idx = tid + it * NT;
+        if ((TOT % NT) == 0 || idx < TOT) {
+          const int l = idx / NX, x = idx % NX;
+          if (l0 + l < a.nlines) {
+            const C u = psi[(long long)(l0 + l) * NX + x];
+            acc += (double)vphi[it] * ((double)u.x * u.x + (double)u.y * u.y);
           }
         }
       }
-      if constexpr (KIND == XP_R) {
-        acc = block_sum(acc, red);
-        if (tid == 0) a.part[bid] = acc;
-        return;
-      }
-      __syncthreads();
-      smem_to_regs_line<C, NX, NT, E, R0>(v, buf);
-      __syncthreads();
+      acc = block_sum(acc, red);
+      if (tid == 0) a.part[bid] = acc;
+      return;
     } else {
-      if constexpr (KIND == XP_R) return;
-      // no nonlocal term: potential phase directly on the first-pass inputs
+      __syncthreads();
 #pragma unroll
-      for (int i = 0; i < E / R0; ++i) {
-        const int w = tid + i * NT, j = w % (NX / R0), l = w / (NX / R0);
-        const int lg = l0 + l;
-#pragma unroll
-        for (int r = 0; r < R0; ++r) {
-          const int pos = j + r * (NX / R0);
+      for (int it = 0; it < PER; ++it) {
+        const int idx = tid + it * NT;
+        if ((TOT % NT) == 0 || idx < TOT) {
+          const int l = idx / NX, x = idx % NX;
+          const int lg = l0 + l;
           C u2 = mk(Real(0), Real(0));
           if (lg < a.nlines) {
-            const C u = psi[(long long)lg * NX + pos];
-            const Real th = Real(a.beta_dt) * (u.x * u.x + u.y * u.y) + trap_phase<Real>(a, pos, lg);
+            const C u = psi[(long long)lg * NX + x];
+            const Real rho = u.x * u.x + u.y * u.y;
+            const Real th = Real(a.beta_dt) * rho + Real(a.lam) * vphi[it] + trap_phase<Real>(a, x, lg);
             Real sn, cs;
             sincos(th, &sn, &cs);
             u2 = unit_mul(u, cs, -sn, false);
@@ -535,83 +542,18 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
               u2 = mk(f * u2.x, f * u2.y);
             }
           }
-          v[i * R0 + r] = u2;
+          buf[x * LDS + l] = u2;
         }
       }
-    }
-    if constexpr (KIND == XP_A) {
-      regs_fft_line<C, NX, NT, E, -1, true, 0, 1>(v, buf, twn);
-#pragma unroll
-      for (int i = 0; i < E / RL; ++i) {
-        const int w = tid + i * NT, j = w % (NX / RL), l = w / (NX / RL);
-        if (l0 + l < a.nlines) {
-#pragma unroll
-          for (int r = 0; r < RL; ++r) psi[(long long)(l0 + l) * NX + j + r * (NX / RL)] = v[i * RL + r];
+      __syncthreads();
+      fft_tile<C, NX, NCOL, NT, -1, true>(buf, twn);
+#pragma unroll 8
+      for (int it = 0; it < PER; ++it) {
+        const int idx = tid + it * NT;
+        if ((TOT % NT) == 0 || idx < TOT) {
+          const int l = idx / NX, x = idx % NX;
+          if (l0 + l < a.nlines) psi[(long long)(l0 + l) * NX + x] = buf[x * LDS + l];
         }
-      }
-    }
-  } else if constexpr (KIND == XP_ADJ1 || KIND == XP_ADJ2) {
-    // adjoint pass 1: g_u2 (in psi) -> h = exp(+i Theta) g_u2 (stored in psi),
-    //   r = Im(conj(g_u2) u2) -> x-half-spectra of r in S, trap-gradient partials;
-    // adjoint pass 2: g_u1 = h + 2 q u1, q = dt beta r + lambda Kc r, r = Im(conj(h) u1)
-    const C* u1p = reinterpret_cast<const C*>(a.aux);
-    C z[E];
-    if (a.use_spec) c2r_pairs<Real, NX>(a, buf, l0, tw2n, z);
-    double dg0 = 0.0, dg1 = 0.0, dg2 = 0.0;
-    // pointwise work on (pair q, position pos) items: from the packed transform's
-    // last radix when varphi (or Kc r) is needed, else a plain j-fastest sweep
-    constexpr int NI = (E / QL) * QL;
-    if (a.use_spec) __syncthreads();
-#pragma unroll
-    for (int e = 0; e < NI; ++e) {
-      const int i = e / QL, r = e % QL;
-      const int w = tid + i * NT, j = w % (N2 / QL), q = w / (N2 / QL);
-      const int pos = j + r * (N2 / QL);
-      if (pos >= NX) continue;
-      const C zz = a.use_spec ? z[e] : mk(Real(0), Real(0));
-      C rpack = mk(Real(0), Real(0));
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int lg = l0 + 2 * q + h;
-        const Real fld = h ? zz.y : zz.x;
-        if (lg >= a.nlines) continue;
-        const long long o = (long long)lg * NX + pos;
-        const C u = u1p[o];
-        const C g = psi[o];
-        if constexpr (KIND == XP_ADJ1) {
-          const Real th = Real(a.beta_dt) * (u.x * u.x + u.y * u.y) + Real(a.lam) * fld + trap_phase<Real>(a, pos, lg);
-          Real sn, cs;
-          sincos(th, &sn, &cs);
-          const C u2 = mk(u.x * cs + u.y * sn, u.y * cs - u.x * sn);
-          const Real rr = g.x * u2.y - g.y * u2.x;
-          if (h) rpack.y = rr; else rpack.x = rr;
-          psi[o] = mk(g.x * cs - g.y * sn, g.y * cs + g.x * sn);
-          const double X = a.lo0 + a.h0 * pos, Y = a.lo1 + a.h1 * (lg % a.ny), Z = a.lo2 + a.h2 * (lg / a.ny);
-          dg0 += (double)rr * (a.dp[0] * X * X + a.dp[1] * Y * Y + a.dp[2] * X * Y + a.dp[3] * Z * Z);
-          dg1 += (double)rr * (a.dp[4] * X * X + a.dp[5] * Y * Y + a.dp[6] * X * Y + a.dp[7] * Z * Z);
-          dg2 += (double)rr * (a.dp[8] * X * X + a.dp[9] * Y * Y + a.dp[10] * X * Y + a.dp[11] * Z * Z);
-        } else {
-          const Real rr = g.x * u.y - g.y * u.x;
-          const Real q2 = Real(2) * (Real(a.beta_dt) * rr + Real(a.lam) * fld);
-          psi[o] = mk(g.x + q2 * u.x, g.y + q2 * u.y);
-        }
-      }
-      if constexpr (KIND == XP_ADJ1) {
-        if (a.use_spec) buf[lidx(LS2, q, pos)] = rpack;
-      }
-    }
-    if constexpr (KIND == XP_ADJ1) {
-      if (a.part) {
-        dg0 = block_sum(dg0, red);
-        if (tid == 0) a.part[bid] = dg0;
-        dg1 = block_sum(dg1, red);
-        if (tid == 0) a.part[a.part_stride + bid] = dg1;
-        dg2 = block_sum(dg2, red);
-        if (tid == 0) a.part[2 * a.part_stride + bid] = dg2;
-      }
-      if (a.use_spec) {
-        __syncthreads();
-        r2c_pairs_from_smem<Real, NX>(a, buf, l0, tw2n);
       }
     }
   }

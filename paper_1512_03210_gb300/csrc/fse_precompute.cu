@@ -48,20 +48,21 @@ __global__ void k_twiddles(typename Cplx<Real>::T* tw, int L) {
 }
 
 // Kinetic multipliers exp(-i theta_k) (half step, theta = dt/4 (|k|^2+m^2)^s)
-// and exp(-2 i theta_k) (two merged half steps) in the field's layout
-// [nz][ny][nx] with wrapped mode numbers; float64 arithmetic, rounded to the
-// plan's precision with the norm-closest float pair (see round_pair).
+// and exp(-2 i theta_k) (two merged half steps) on the octant of mode
+// magnitudes |p_j| = 0..n_j/2, layout [nz/2+1][ny/2+1][nx/2+1]: theta depends
+// on |k| only, so every sign combination shares one entry (17 MB at 256^3,
+// resident in L2). float64 arithmetic, rounded to the plan's precision with the
+// norm-closest float pair (see round_pair).
 template <typename Real>
 __global__ void k_kin_table(typename Cplx<Real>::T* half, typename Cplx<Real>::T* full, int nx, int ny, int nz,
                             double dkx, double dky, double dkz, double s, double m2, double dt) {
-  const long long N = (long long)nx * ny * nz;
+  const int hx = nx / 2 + 1, hy = ny / 2 + 1, hz = nz > 1 ? nz / 2 + 1 : 1;
+  const long long N = (long long)hx * hy * hz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(i % nx);
-    const long long r = i / nx;
-    const int iy = (int)(r % ny), iz = (int)(r / ny);
-    const double kx = dkx * (ix < nx / 2 ? ix : ix - nx);
-    const double ky = dky * (iy < ny / 2 ? iy : iy - ny);
-    const double kz = nz > 1 ? dkz * (iz < nz / 2 ? iz : iz - nz) : 0.0;
+    const int ix = (int)(i % hx);
+    const long long r = i / hx;
+    const int iy = (int)(r % hy), iz = (int)(r / hy);
+    const double kx = dkx * ix, ky = dky * iy, kz = dkz * iz;
     const double k2 = kx * kx + ky * ky + kz * kz + m2;
     const double th = 0.25 * dt * (k2 > 0.0 ? pow(k2, s) : 0.0);
     double sn, cs;
