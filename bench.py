@@ -231,6 +231,22 @@ def run_reference(args, rank: int):
     return 0
 
 
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """Slowest rank's timed-region length (ms); the job is done when it is."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_value(steps: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput: every replica advances its own grid `steps` times."""
+    return world * steps / (ms_max / 1000.0)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -300,12 +316,8 @@ def main():
     barrier()
     launches = plan.launches - l0
     t += args.steps * d["dt"]
-    ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * args.steps / (ms / 1000.0)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev)
+    value = job_value(args.steps, ms, world)
 
     # per-kernel event timing over a second region of the same length
     fse.fse_plan_profile(plan.handle, True)

@@ -57,6 +57,11 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// Bulk prefetch of a contiguous global range into L2 (address and size
+// multiples of 16 bytes); no completion to wait for.
+__device__ __forceinline__ void prefetch_l2_bulk(const void* gmem, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(gmem), "r"(bytes) : "memory");
+}
 
 // ---------------------------------------------------------------------------
 // Radix plans: N = 2^a 3^b (b <= 1) split into passes of radix 3, 8, 4, 2.
@@ -134,21 +139,27 @@ template <> struct Kc<double> {
 __device__ __forceinline__ float mulk(float x, float k1, float k2) { return fmaf(x, k1, x * k2); }
 __device__ __forceinline__ double mulk(double x, double k1, double) { return x * k1; }
 
-template <int DIR, typename C> __device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
+// Product by a butterfly constant: two-term (EXACT) or the rounded head alone.
+template <bool EXACT, typename R> __device__ __forceinline__ R kmul(R x, R k1, R k2) {
+  if constexpr (EXACT) return mulk(x, k1, k2);
+  else return x * k1;
+}
+
+template <int DIR, bool EXACT, typename C> __device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
   typedef decltype(a0.x) R;
   const R c = R(-0.5);
   C t = cadd(a1, a2);
   C d = csub(a1, a2);
   C m = mk(a0.x + c * t.x, a0.y + c * t.y);
   // i * DIR * sin(2 pi/3) * (a1 - a2): exp(DIR 2 pi i/3) = c + i DIR sin(2 pi/3)
-  const R sy = mulk(d.y, Kc<R>::s1, Kc<R>::s2), sx = mulk(d.x, Kc<R>::s1, Kc<R>::s2);
+  const R sy = kmul<EXACT>(d.y, Kc<R>::s1, Kc<R>::s2), sx = kmul<EXACT>(d.x, Kc<R>::s1, Kc<R>::s2);
   C e = DIR < 0 ? mk(sy, -sx) : mk(-sy, sx);
   a0 = cadd(a0, t);
   a1 = cadd(m, e);
   a2 = csub(m, e);
 }
 
-template <int DIR, typename C> __device__ __forceinline__ void dft8(C* v) {
+template <int DIR, bool EXACT, typename C> __device__ __forceinline__ void dft8(C* v) {
   typedef decltype(v[0].x) R;
   // even / odd halves
   dft4<DIR>(v[0], v[2], v[4], v[6]);
@@ -158,9 +169,9 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8(C* v) {
   C o1 = v[3], o2 = v[5], o3 = v[7];
   const R a1 = o1.x - R(DIR) * o1.y, b1 = o1.y + R(DIR) * o1.x;
   const R a3 = -o3.x - R(DIR) * o3.y, b3 = -o3.y + R(DIR) * o3.x;
-  C t1 = mk(mulk(a1, Kc<R>::h1, Kc<R>::h2), mulk(b1, Kc<R>::h1, Kc<R>::h2));
+  C t1 = mk(kmul<EXACT>(a1, Kc<R>::h1, Kc<R>::h2), kmul<EXACT>(b1, Kc<R>::h1, Kc<R>::h2));
   C t2 = mul_i<DIR>(o2);
-  C t3 = mk(mulk(a3, Kc<R>::h1, Kc<R>::h2), mulk(b3, Kc<R>::h1, Kc<R>::h2));
+  C t3 = mk(kmul<EXACT>(a3, Kc<R>::h1, Kc<R>::h2), kmul<EXACT>(b3, Kc<R>::h1, Kc<R>::h2));
   C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
   v[0] = cadd(e0, o0);
   v[4] = csub(e0, o0);
@@ -172,16 +183,18 @@ template <int DIR, typename C> __device__ __forceinline__ void dft8(C* v) {
   v[7] = csub(e3, t3);
 }
 
-template <int R, int DIR, typename C> __device__ __forceinline__ void dft(C* v) {
+// EXACT = false drops the tails of the irrational constants (transforms of the
+// density and potential, where a fixed 1e-8 scale error is harmless).
+template <int R, int DIR, bool EXACT = true, typename C> __device__ __forceinline__ void dft(C* v) {
   if constexpr (R == 2) {
     dft2<DIR>(v[0], v[1]);
   } else if constexpr (R == 3) {
-    dft3<DIR>(v[0], v[1], v[2]);
+    dft3<DIR, EXACT>(v[0], v[1], v[2]);
   } else if constexpr (R == 4) {
     dft4<DIR>(v[0], v[1], v[2], v[3]);
   } else {
     static_assert(R == 8, "radix");
-    dft8<DIR>(v);
+    dft8<DIR, EXACT>(v);
   }
 }
 
@@ -249,7 +262,7 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
 #pragma unroll
         for (int r = 1; r < R; ++r) v[it][r] = twiddle_mul<DIR, EXACT>(v[it][r], tw, (k * r) * (N / (NS * R)));
       }
-      dft<R, DIR>(v[it]);
+      dft<R, DIR, EXACT>(v[it]);
     }
   }
   __syncthreads();
@@ -325,7 +338,7 @@ __device__ __forceinline__ void regs_pass(C (&v)[E], const C* __restrict__ tw) {
 #pragma unroll
       for (int r = 1; r < R; ++r) v[i * R + r] = twiddle_mul<DIR, EXACT>(v[i * R + r], tw, (k * r) * (N / (NS * R)));
     }
-    dft<R, DIR>(&v[i * R]);
+    dft<R, DIR, EXACT>(&v[i * R]);
   }
 }
 
@@ -354,20 +367,29 @@ __device__ __forceinline__ void smem_to_regs(C (&v)[E], const C* buf) {
   }
 }
 
+// Radix of pass p of the plan for N, taken in reverse order when REV is set.
+template <int N, bool REV>
+__host__ __device__ constexpr int plan_radix(int p) {
+  return REV ? radix_plan(N).r[radix_plan(N).npass - 1 - p] : radix_plan(N).r[p];
+}
+
 // Runs passes PASS..last on v (holding the inputs of pass PASS). On return v
-// holds the outputs of the last pass at positions j + r N/R_last.
-template <typename C, int N, int NCOL, int NT, int E, int DIR, bool EXACT, int PASS, int NS>
+// holds the outputs of the last pass at positions j + r N/R_last. With REV the
+// radices are taken in reverse order: a transform whose inputs are the outputs
+// of a forward-order transform (positions j + r N/R_last) then starts without an
+// exchange, since its first radix is that transform's last one.
+template <typename C, int N, int NCOL, int NT, int E, int DIR, bool EXACT, int PASS, int NS, bool REV = false>
 __device__ __forceinline__ void regs_fft(C (&v)[E], C* buf, const C* __restrict__ tw) {
-  constexpr RadixPlan P = radix_plan(N);
-  constexpr int R = P.r[PASS];
+  constexpr int NP = radix_plan(N).npass;
+  constexpr int R = plan_radix<N, REV>(PASS);
   regs_pass<C, N, NCOL, NT, E, DIR, EXACT, R, NS>(v, tw);
-  if constexpr (PASS + 1 < P.npass) {
-    constexpr int R2 = P.r[PASS + 1];
+  if constexpr (PASS + 1 < NP) {
+    constexpr int R2 = plan_radix<N, REV>(PASS + 1);
     regs_to_smem<C, N, NCOL, NT, E, R, NS>(v, buf);
     __syncthreads();
     smem_to_regs<C, N, NCOL, NT, E, R2>(v, buf);
     __syncthreads();
-    regs_fft<C, N, NCOL, NT, E, DIR, EXACT, PASS + 1, NS * R>(v, buf, tw);
+    regs_fft<C, N, NCOL, NT, E, DIR, EXACT, PASS + 1, NS * R, REV>(v, buf, tw);
   }
 }
 

@@ -140,18 +140,29 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
                                              const typename Cplx<Real>::T* __restrict__ tw, int bid) {
   typedef ColCfg<Real, N> K;
   typedef typename K::C C;
-  constexpr int NCOL = K::NCOL, NT = K::NT, E = K::E, R0 = K::R0, RL = K::RL, LDS = NCOL + 1;
-  // rows >= N/2 of a zero-padded input are inputs r >= R0/2 of the first pass (and
-  // outputs r >= RL/2 of the last pass) only when that radix is even
-  constexpr bool HALF_IN = (VAR == COL_PADF || VAR == COL_KHAT) && (R0 % 2 == 0);
-  constexpr bool HALF_OUT = (VAR == COL_CROPI || VAR == COL_KHAT) && (RL % 2 == 0);
+  constexpr int NCOL = K::NCOL, NT = K::NT, E = K::E, R0 = K::R0, RL = K::RL;
+  // forward . multiplier . inverse variants run the inverse with the radices
+  // reversed, so it starts on the forward's outputs as they sit in registers;
+  // the final outputs are then at positions j + r N/R0
+  constexpr bool FUSED = (VAR == COL_KIN || VAR == COL_KHAT);
+  constexpr int RF = FUSED ? R0 : RL;
+  // input r of the first pass (output r of the last) lies at rows >= N/2 for
+  // every j when 2 r >= R: zero in a zero-padded input, dropped by the crop
+  constexpr bool HALF_IN = (VAR == COL_PADF || VAR == COL_KHAT);
+  constexpr bool HALF_OUT = (VAR == COL_CROPI || VAR == COL_KHAT);
   constexpr bool EXACT = (VAR == COL_FWD || VAR == COL_INV || VAR == COL_KIN);
   constexpr int DIR1 = (VAR == COL_INV || VAR == COL_CROPI) ? +1 : -1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int tid = threadIdx.x;
-  const int plane = bid / a.tiles_per_plane;
-  const int c0 = (bid - plane * a.tiles_per_plane) * NCOL;
+  const int tp = bid / a.tiles_per_plane;
+  const int c0 = (bid - tp * a.tiles_per_plane) * NCOL;
+  // kernel-transform pass over a full even set of planes: planes p and lp - p
+  // (same |p|, same C^ values) run next to each other, so the octant is read
+  // from HBM about once
+  const int plane = (VAR == COL_KHAT && m.lp == a.nplanes && (m.lp & 1) == 0 && tp > 0)
+                        ? ((tp & 1) ? (tp + 1) >> 1 : m.lp - (tp >> 1))
+                        : tp;
   C* base = reinterpret_cast<C*>(a.data) + (long long)plane * a.plane_stride + c0;
   const int ncv = min(NCOL, a.ncols - c0);
   C v[E];
@@ -176,7 +187,7 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
 #pragma unroll
     for (int r = 0; r < R0; ++r) {
       const int row = j + r * (N / R0);
-      if (HALF_IN && r >= R0 / 2) {
+      if (HALF_IN && 2 * r >= R0) {
         v[i * R0 + r] = mk(Real(0), Real(0));  // rows >= N/2 of a zero-padded line
       } else {
         v[i * R0 + r] = (row < a.n_load && c < ncv) ? base[(long long)row * a.line_stride + c] : mk(Real(0), Real(0));
@@ -201,8 +212,8 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
         for (int r = 0; r < RL; ++r) {
           const int row = j + r * (N / RL);
           const C t = c < ncv ? __ldg(&tab[(long long)abs(wrap_index(row, m.lr)) * m.kin_sr + ax]) : mk(Real(1), Real(0));
-          C x = unit_mul(v[i * RL + r], t.x, t.y, m.conj != 0);
-          buf[row * LDS + c] = mk(sc * x.x, sc * x.y);
+          const C x = unit_mul(v[i * RL + r], t.x, t.y, m.conj != 0);
+          v[i * RL + r] = mk(sc * x.x, sc * x.y);
         }
       }
     } else {
@@ -237,24 +248,22 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
             f = Real(m.a0) * cv;
           }
           const C x = v[i * RL + r];
-          buf[row * LDS + c] = mk(f * x.x, f * x.y);
+          v[i * RL + r] = mk(f * x.x, f * x.y);
         }
       }
     }
-    __syncthreads();
-    smem_to_regs<C, N, NCOL, NT, E, R0>(v, buf);
-    __syncthreads();
-    regs_fft<C, N, NCOL, NT, E, +1, EXACT, 0, 1>(v, buf, tw);
+    // the last exchange of the forward transform ended with a barrier, so buf is free
+    regs_fft<C, N, NCOL, NT, E, +1, EXACT, 0, 1, true>(v, buf, tw);
   }
   // outputs of the last pass to global memory (rows >= n_store cropped)
 #pragma unroll
-  for (int i = 0; i < E / RL; ++i) {
+  for (int i = 0; i < E / RF; ++i) {
     const int w = tid + i * NT, c = w % NCOL, j = w / NCOL;
 #pragma unroll
-    for (int r = 0; r < RL; ++r) {
-      const int row = j + r * (N / RL);
-      if (HALF_OUT && r >= RL / 2) continue;  // rows >= N/2 are cropped
-      if (row < a.n_store && c < ncv) base[(long long)row * a.line_stride + c] = v[i * RL + r];
+    for (int r = 0; r < RF; ++r) {
+      const int row = j + r * (N / RF);
+      if (HALF_OUT && 2 * r >= RF) continue;  // rows >= N/2 are cropped
+      if (row < a.n_store && c < ncv) base[(long long)row * a.line_stride + c] = v[i * RF + r];
     }
   }
 }
@@ -343,14 +352,19 @@ __device__ __forceinline__ void c2r_rows(const XArgs& a, typename Cplx<Real>::T*
   constexpr int NCOL = K::NCOL, NT = K::NT, LDS2 = K::LDS2, TOT = K::TOT, PER = K::PER;
   const int tid = threadIdx.x;
   const C* S = reinterpret_cast<const C*>(a.spec);
-  for (int idx = tid; idx < (NCOL / 2) * (NX + 1); idx += NT) {
-    const int q = idx / (NX + 1), k = idx % (NX + 1);
-    const int la = l0 + 2 * q;
-    C A = mk(Real(0), Real(0)), B = A;
-    if (la < a.nlines) A = S[srow(la, a.ny, a.srow_mul) * a.sx + k];
-    if (la + 1 < a.nlines) B = S[srow(la + 1, a.ny, a.srow_mul) * a.sx + k];
-    buf[k * LDS2 + q] = mk(A.x - B.y, A.y + B.x);
-    if (k > 0 && k < NX) buf[(2 * NX - k) * LDS2 + q] = mk(A.x + B.y, B.x - A.y);
+  constexpr int NH = (NCOL / 2) * (NX + 1), PH = (NH + NT - 1) / NT;
+#pragma unroll
+  for (int it = 0; it < PH; ++it) {
+    const int idx = tid + it * NT;
+    if (idx < NH) {
+      const int q = idx / (NX + 1), k = idx % (NX + 1);
+      const int la = l0 + 2 * q;
+      C A = mk(Real(0), Real(0)), B = A;
+      if (la < a.nlines) A = S[srow(la, a.ny, a.srow_mul) * a.sx + k];
+      if (la + 1 < a.nlines) B = S[srow(la + 1, a.ny, a.srow_mul) * a.sx + k];
+      buf[k * LDS2 + q] = mk(A.x - B.y, A.y + B.x);
+      if (k > 0 && k < NX) buf[(2 * NX - k) * LDS2 + q] = mk(A.x + B.y, B.x - A.y);
+    }
   }
   __syncthreads();
   fft_tile<C, 2 * NX, NCOL / 2, NT, +1, false>(buf, tw2n);
@@ -365,6 +379,21 @@ __device__ __forceinline__ void c2r_rows(const XArgs& a, typename Cplx<Real>::T*
     }
   }
 }
+
+// sin and cos of a potential phase. For |th| <= 1/2 the Taylor series to
+// th^9 / th^8 (truncation below 3e-10) in Horner form; sincos otherwise.
+__device__ __forceinline__ void phase_sincos(float th, float* sn, float* cs) {
+  if (fabsf(th) <= 0.5f) {
+    const float t2 = th * th;
+    const float ps = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 1.0f / 362880.0f, -1.0f / 5040.0f), 1.0f / 120.0f), -1.0f / 6.0f), 0.0f);
+    const float pc = fmaf(t2, fmaf(t2, fmaf(t2, fmaf(t2, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f), -0.5f), 0.0f);
+    *sn = fmaf(th, ps, th);
+    *cs = 1.0f + pc;
+  } else {
+    sincosf(th, sn, cs);
+  }
+}
+__device__ __forceinline__ void phase_sincos(double th, double* sn, double* cs) { sincos(th, sn, cs); }
 
 template <typename Real>
 __device__ __forceinline__ Real trap_phase(const XArgs& a, int x, int lg) {
@@ -500,6 +529,11 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
     }
   } else {
     // XP_A / XP_R: varphi from the cropped C2R of S
+    if (KIND == XP_A && tid == 0 && l0 < a.nlines) {
+      // the tile's rows of psi (contiguous) move to L2 while the C2R runs
+      const int nl = min(NCOL, a.nlines - l0);
+      prefetch_l2_bulk(psi + (long long)l0 * NX, (unsigned)(nl * NX * sizeof(C)));
+    }
     Real vphi[PER];
 #pragma unroll
     for (int it = 0; it < PER; ++it) vphi[it] = Real(0);
@@ -535,7 +569,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
             const Real rho = u.x * u.x + u.y * u.y;
             const Real th = Real(a.beta_dt) * rho + Real(a.lam) * vphi[it] + trap_phase<Real>(a, x, lg);
             Real sn, cs;
-            sincos(th, &sn, &cs);
+            phase_sincos(th, &sn, &cs);
             u2 = unit_mul(u, cs, -sn, false);
             if (a.scale) {
               const Real f = Real(*a.scale);
