@@ -64,7 +64,7 @@ class Params:
 
     FIELDS = dict(dim=2, n=None, lo=None, hi=None, s=1.0, m=0.0, omega=0.0, beta=0.0,
                   lam=0.0, dt=1e-3, kernel="coulomb", mu=1.0, dip_n=(0.0, 0.0, 1.0),
-                  gamma=(1.0, 1.0, 1.0), gs_delta=1e-3, gs_h=0.125, gs_tmin=-36.0)
+                  gamma=(1.0, 1.0, 1.0), gs_delta=1e-3, gs_h=0.125, gs_tmin=None)
 
     def __init__(self, **kw):
         for k, v in self.FIELDS.items():
@@ -76,6 +76,13 @@ class Params:
         self.gamma = g + (1.0,) * (3 - len(g))
         if self.kernel == "ddi3d" and self.dim != 3:
             raise ValueError("the 3D dipolar kernel needs dim=3")
+        if self.kernel == "ddi3d" and self.mu != 1.0:
+            raise ValueError("the 3D dipolar kernel is built on 1/|x| (mu = 1)")
+        if self.kernel == "coulomb" and not (0.0 < self.mu <= self.dim - 1):
+            raise ValueError("Coulomb-type kernel 1/|x|^mu needs 0 < mu <= d - 1 (Eq. Kernel)")
+        if not self.gs_tmin:
+            # lower end of the sinc quadrature: the dropped tail is ~ e^{mu t_min} / mu
+            self.gs_tmin = -36.0 / self.mu
 
     def shape(self):
         """Array shape, x fastest: (ny, nx) or (nz, ny, nx)."""
@@ -262,15 +269,17 @@ def near_field(p, w, tau, panels=16, nodes=20):
     """I0 = int_{B_delta} (U - U_GS) and I2 = int_{B_delta} |y|^2 (U - U_GS).
 
     The two radial integrals of the near-field correction (Eq. taylor), by
-    composite Gauss-Legendre on [0, delta] with the d-dimensional Jacobian.
+    composite Gauss-Legendre with the d-dimensional Jacobian, in u with
+    r = delta u^2 so that r^{d-1-mu} dr stays smooth for non-integer mu.
     """
     p = params(p)
     delta = p.gs_delta * _box_scale(p)
-    edges = np.linspace(0.0, delta, panels + 1)
+    edges = np.linspace(0.0, 1.0, panels + 1)
     xg, wg = np.polynomial.legendre.leggauss(nodes)
     a, b = edges[:-1, None], edges[1:, None]
-    r = (0.5 * (b - a) * xg[None, :] + 0.5 * (a + b)).ravel()
-    wr = (0.5 * (b - a) * wg[None, :]).ravel()
+    u = (0.5 * (b - a) * xg[None, :] + 0.5 * (a + b)).ravel()
+    r = delta * u * u
+    wr = (0.5 * (b - a) * wg[None, :]).ravel() * 2.0 * delta * u
     surf = 2 * math.pi * r if p.dim == 2 else 4 * math.pi * r * r
     U = _kernel_prefactor(p) * r ** (-p.mu)
     Ugs = np.exp(-np.outer(r * r, tau * tau)) @ w

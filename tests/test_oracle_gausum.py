@@ -248,3 +248,71 @@ def test_dipole_integral_quadrature():
     # m(t) = A(t)^{-1} n rotates the in-plane part backwards
     m = O.dipole_axis(p, math.pi / (2 * p.omega))
     assert np.allclose(m, [0.0, 1 / math.sqrt(2), 1 / math.sqrt(2)], atol=1e-15)
+
+
+# --- Coulomb-type kernels 1/|x|^mu, 0 < mu <= d - 1 (Eq. Kernel) --------------------
+
+MU_CASES = [(2, 0.5), (2, 1.0), (3, 0.5), (3, 1.5), (3, 2.0)]
+
+
+@pytest.mark.parametrize("d,mu", MU_CASES)
+def test_gausum_fit_accuracy_mu(d, mu):
+    """U_GS within 1e-13 (relative) of 1/(2^{d-1} pi r^mu) on [delta, 2 sqrt(d)] (Eq. GS-Gene)."""
+    p = O.Params(dim=d, n=(16,) * d, lo=(-1.0,) * d, hi=(1.0,) * d, kernel="coulomb", mu=mu)
+    w, tau = O.gausum_nodes(p)
+    r = np.geomspace(p.gs_delta, 2 * math.sqrt(d), 400)
+    ugs = np.exp(-np.outer(r * r, tau * tau)) @ w
+    u = 1.0 / (2 ** (d - 1) * math.pi * r ** mu)
+    assert np.max(np.abs(ugs / u - 1)) < 1e-13
+
+
+@pytest.mark.parametrize("d,mu", MU_CASES)
+def test_near_field_integrals_closed_form_mu(d, mu):
+    """I0, I2 for 1/|x|^mu against exact radial integrals (incomplete gamma, 40 digits)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    p = O.Params(dim=d, n=(16,) * d, lo=(-3.0,) * d, hi=(3.0,) * d, kernel="coulomb", mu=mu)
+    w, tau = O.gausum_nodes(p)
+    I0, I2 = O.near_field(p, w, tau)
+    dl = mp.mpf(p.gs_delta) * 3
+    S = 2 * mp.pi if d == 2 else 4 * mp.pi
+    pref = 1 / (2 ** (d - 1) * mp.pi)
+    m = mp.mpf(mu)
+
+    def gint(j, t):
+        t = mp.mpf(t)
+        return mp.gammainc(mp.mpf(j + 1) / 2, 0, (t * dl) ** 2) / (2 * t ** (j + 1))
+    u0 = pref * S * dl ** (d - m) / (d - m)
+    u2 = pref * S * dl ** (d + 2 - m) / (d + 2 - m)
+    e0 = u0 - S * mp.fsum(mp.mpf(wq) * gint(d - 1, tq) for wq, tq in zip(w, tau))
+    e2 = u2 - S * mp.fsum(mp.mpf(wq) * gint(d + 1, tq) for wq, tq in zip(w, tau))
+    assert abs(I0 - float(e0)) < 1e-12 * float(u0)
+    assert abs(I2 - float(e2)) < 1e-12 * float(u2)
+
+
+@pytest.mark.parametrize("d,mu,n,L", [(2, 0.5, 64, 8.0), (3, 1.5, 48, 6.0), (3, 0.5, 48, 6.0)])
+def test_riesz_potential_of_gaussian_closed_form(d, mu, n, L):
+    """rho = pi^{-d/2} e^{-r^2}: int rho(y)/|x-y|^mu dy = Gamma((d-mu)/2)/Gamma(d/2) 1F1(mu/2; d/2; -r^2).
+
+    At mu = 1 this is erf(r)/r (3D) and sqrt(pi) e^{-r^2/2} I0(r^2/2) (2D),
+    the two Coulomb closed forms above."""
+    p = O.Params(dim=d, n=(n,) * d, lo=(-L,) * d, hi=(L,) * d, kernel="coulomb", mu=mu)
+    X = O.coords(p)
+    r2 = sum(X[j] ** 2 for j in range(d))
+    rho = math.pi ** (-d / 2) * np.exp(-r2)
+    Phi = O.nonlocal_potential(rho, p, O.gausum_multiplier(p))
+    ex = (special.gamma((d - mu) / 2) / special.gamma(d / 2) * special.hyp1f1(mu / 2, d / 2, -r2)
+          / (2 ** (d - 1) * math.pi))
+    assert np.max(np.abs(Phi - ex)) < 1e-12 * np.max(np.abs(ex))
+
+
+def test_kernel_exponent_range():
+    """Eq. Kernel: 0 < mu <= d - 1 for the Coulomb type; the dipolar kernel uses mu = 1."""
+    base = dict(n=(8, 8), lo=(-1.0, -1.0), hi=(1.0, 1.0), kernel="coulomb")
+    for bad in (0.0, 1.5, -1.0):
+        with pytest.raises(ValueError):
+            O.Params(dim=2, mu=bad, **base)
+    assert O.Params(dim=2, mu=1.0, **base).gs_tmin == -36.0
+    assert O.Params(dim=2, mu=0.5, **base).gs_tmin == -72.0
+    with pytest.raises(ValueError):
+        O.Params(dim=3, n=(8,) * 3, lo=(-1.0,) * 3, hi=(1.0,) * 3, kernel="ddi3d", mu=0.5)
