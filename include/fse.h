@@ -59,12 +59,13 @@ typedef enum { FSE_F32 = 0, FSE_F64 = 1 } fse_prec;
  *   lambda     nonlocal interaction strength
  *   dt         time step (may be negative: the scheme is time-reversible)
  *   kernel     fse_kernel: none, Coulomb-type 1/(2^{d-1} pi |x|^mu), or 3D DDI
- *   mu         Coulomb exponent; this build supports mu = 1
+ *   mu         exponent of the Coulomb-type kernel, 0 < mu <= dim - 1 (Eq.
+ *              Kernel); the 3D DDI kernel is built on mu = 1
  *   dip_n[3]   dipole axis n (unit vector) for FSE_KERNEL_DDI3D
  *   gamma[3]   harmonic trap frequencies (Eq. harm_poten)
  *   gs_delta, gs_h, gs_tmin  Gaussian-sum fit (Eq. GS-Gene): near-field
  *              radius in unit-box units, sinc-quadrature step and lower
- *              end; 0 selects 1e-3, 0.125, -36
+ *              end; 0 selects 1e-3, 0.125, -36/mu
  *   prec       fse_prec: arithmetic of the split step
  *   renormalize  0: the paper's scheme; 1: after each step rescale psi so that
  *              its float64 mass equals the mass at the start of the fse_step
@@ -96,8 +97,9 @@ typedef struct {
  * = legacy default stream) on the current CUDA device, and return in
  * *workspace_bytes the size of the device workspace the caller must supply.
  * Errors: FSE_ERR_INVALID (null pointers, dim, s <= 0, box, dt = 0, kernel
- * and dim mismatch), FSE_ERR_UNSUPPORTED (a size outside the supported set,
- * mu != 1). On error *out is NULL. */
+ * and dim mismatch, mu outside (0, dim - 1] for the Coulomb-type kernel or
+ * mu != 1 for the DDI kernel), FSE_ERR_UNSUPPORTED (a size outside the
+ * supported set). On error *out is NULL. */
 fse_status fse_plan_create(const fse_params* params, void* cuda_stream, fse_plan_t* out,
                            size_t* workspace_bytes);
 

@@ -234,6 +234,19 @@ int tiles(fse_plan* P, int N, int ncols) {
   return (ncols + nc - 1) / nc;
 }
 
+// Passes over the R2C bins 0..nx of many planes: the last, nearly empty tile
+// of every plane (nx + 1 = k NCOL + 1 bins for the usual sizes) is replaced by
+// tail tiles holding that column of NCOL planes each.
+ColArgs with_tail(fse_plan* P, ColArgs a, int N) {
+  const int nc = P->prec == FSE_F32 ? colpass_ncol<float>(N) : colpass_ncol<double>(N);
+  const int rem = a.ncols % nc;
+  if (a.nplanes > 1 && rem > 0 && 2 * rem <= nc) {
+    a.tiles_per_plane = a.ncols / nc;
+    a.tail = rem;
+  }
+  return a;
+}
+
 XArgs x_args(fse_plan* P, void* psi, void* spec) {
   XArgs a;
   std::memset(&a, 0, sizeof(a));
@@ -318,7 +331,7 @@ fse_status nonlocal_yz(fse_plan* P, void* spec, double ta, double tb, bool integ
   }
   ColArgs af{spec, (long long)2 * P->ny * P->sx, P->sx, P->nz, P->nx + 1, P->ny, 2 * P->ny,
              tiles(P, 2 * P->ny, P->nx + 1)};
-  if ((st = col(P, FSE_PASS_PAD, 2 * P->ny, COL_PADF, af, m)) != FSE_OK) return st;
+  if ((st = col(P, FSE_PASS_PAD, 2 * P->ny, COL_PADF, with_tail(P, af, 2 * P->ny), m)) != FSE_OK) return st;
   m.lp = 2 * P->ny;
   m.dkp = 2 * kPi / (2.0 * (P->p.hi[1] - P->p.lo[1]));
   m.lr = 2 * P->nz;
@@ -345,10 +358,10 @@ fse_status nonlocal_yz(fse_plan* P, void* spec, double ta, double tb, bool integ
   }
   ColArgs ag{spec, P->sx, (long long)2 * P->ny * P->sx, 2 * P->ny, P->nx + 1, P->nz, P->nz,
              tiles(P, 2 * P->nz, P->nx + 1)};
-  if ((st = col(P, FSE_PASS_KHAT, 2 * P->nz, COL_KHAT, ag, m)) != FSE_OK) return st;
+  if ((st = col(P, FSE_PASS_KHAT, 2 * P->nz, COL_KHAT, with_tail(P, ag, 2 * P->nz), m)) != FSE_OK) return st;
   ColArgs ah{spec, (long long)2 * P->ny * P->sx, P->sx, P->nz, P->nx + 1, 2 * P->ny, P->ny,
              tiles(P, 2 * P->ny, P->nx + 1)};
-  return col(P, FSE_PASS_PAD, 2 * P->ny, COL_CROPI, ah, m);
+  return col(P, FSE_PASS_PAD, 2 * P->ny, COL_CROPI, with_tail(P, ah, 2 * P->ny), m);
 }
 
 bool has_nonlocal(const fse_plan* P) { return P->p.kernel != FSE_KERNEL_NONE && P->p.lambda != 0.0; }
@@ -431,14 +444,17 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
     if (!(p.hi[j] > p.lo[j])) return FSE_ERR_INVALID;
     if (!size_supported(p.n[j])) return FSE_ERR_UNSUPPORTED;
   }
-  if (p.kernel == FSE_KERNEL_COULOMB && p.mu != 1.0) return FSE_ERR_UNSUPPORTED;
+  if (p.kernel == FSE_KERNEL_COULOMB && !(p.mu > 0.0 && p.mu <= p.dim - 1)) return FSE_ERR_INVALID;
+  if (p.kernel == FSE_KERNEL_DDI3D && p.mu != 1.0) return FSE_ERR_INVALID;
   if (p.renormalize != 0 && p.renormalize != 1) return FSE_ERR_INVALID;
   fse_plan* P = new (std::nothrow) fse_plan();
   if (!P) return FSE_ERR_NOMEM;
   P->p = p;
   if (P->p.gs_delta <= 0) P->p.gs_delta = 1e-3;
   if (P->p.gs_h <= 0) P->p.gs_h = 0.125;
-  if (P->p.gs_tmin == 0) P->p.gs_tmin = -36.0;
+  if (P->p.kernel == FSE_KERNEL_NONE) P->p.mu = 1.0;
+  // the dropped tail of the sinc quadrature is ~ e^{mu t_min} / mu
+  if (P->p.gs_tmin == 0) P->p.gs_tmin = -36.0 / P->p.mu;
   P->stream = reinterpret_cast<cudaStream_t>(stream);
   cudaGetDevice(&P->device);
   P->dim = p.dim;
@@ -451,18 +467,20 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
   for (int j = 0; j < 3; ++j) P->h[j] = j < p.dim ? (p.hi[j] - p.lo[j]) / p.n[j] : 0.0;
   P->sx = ((P->nx + 1 + 15) / 16) * 16;
 
-  // Gaussian-sum nodes (Eq. GS-Gene): sinc quadrature in unit-box units, scaled.
+  // Gaussian-sum nodes (Eq. GS-Gene): sinc quadrature of
+  // r^-mu = (2 / Gamma(mu/2)) int exp(mu t - r^2 e^{2t}) dt in unit-box units, scaled.
   double wmax = 0.0;
   for (int j = 0; j < p.dim; ++j) wmax = std::fmax(wmax, p.hi[j] - p.lo[j]);
   const double sc = 0.5 * wmax;
   const double tmax = std::log(7.0 / P->p.gs_delta);
   const int Q = (int)std::ceil((tmax - P->p.gs_tmin) / P->p.gs_h) + 1;
   const double pref = 1.0 / (std::pow(2.0, p.dim - 1) * kPi);
+  const double mu = P->p.mu;
   P->gs_w.resize(Q);
   P->gs_tau.resize(Q);
   for (int q = 0; q < Q; ++q) {
     const double t = P->p.gs_tmin + P->p.gs_h * q;
-    P->gs_w[q] = pref * (2.0 * P->p.gs_h / std::sqrt(kPi)) * std::exp(t) / sc;
+    P->gs_w[q] = pref * (2.0 * P->p.gs_h / std::tgamma(0.5 * mu)) * std::exp(mu * t) / std::pow(sc, mu);
     P->gs_tau[q] = std::exp(t) / sc;
   }
   // Near-field integrals I0, I2 over the ball of radius delta (Eq. taylor).
@@ -477,13 +495,10 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
       s2 += P->gs_w[q] * radial_gauss_moment(4, P->gs_tau[q], del);
     }
   }
-  if (p.dim == 2) {
-    P->I0 = del - 2.0 * kPi * s0;
-    P->I2 = del * del * del / 3.0 - 2.0 * kPi * s2;
-  } else {
-    P->I0 = del * del / 2.0 - 4.0 * kPi * s0;
-    P->I2 = del * del * del * del / 4.0 - 4.0 * kPi * s2;
-  }
+  // kernel part: pref * |S^{d-1}| * int_0^delta r^{d-1-mu} (1, r^2) dr
+  const double sd = p.dim == 2 ? 2.0 * kPi : 4.0 * kPi, dd = p.dim;
+  P->I0 = pref * sd * std::pow(del, dd - mu) / (dd - mu) - sd * s0;
+  P->I2 = pref * sd * std::pow(del, dd + 2.0 - mu) / (dd + 2.0 - mu) - sd * s2;
   gauss_legendre(16, P->gl_x, P->gl_w);
 
   // Workspace layout.

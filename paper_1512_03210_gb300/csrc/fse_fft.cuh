@@ -57,6 +57,11 @@ __device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(BYTES) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most N committed groups of this thread are still in flight
+template <int N> __device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 // Bulk prefetch of a contiguous global range into L2 (address and size
 // multiples of 16 bytes); no completion to wait for.
 __device__ __forceinline__ void prefetch_l2_bulk(const void* gmem, unsigned bytes) {
@@ -209,12 +214,13 @@ __device__ __forceinline__ float norm_err(float c, float s) {
   return ((pa - 1.0f) + pb) + (ea + eb);
 }
 
-// v times twiddle m of the table (conjugated for the inverse transform).
-template <int DIR, bool EXACT, typename C>
+// v times twiddle m of the table (conjugated for the inverse transform); the
+// table is in global memory, or in shared memory when TWS is set.
+template <int DIR, bool EXACT, bool TWS = false, typename C>
 __device__ __forceinline__ C twiddle_mul(C v, const C* __restrict__ tw, int m) {
-  const C w = __ldg(&tw[2 * m]);
+  const C w = TWS ? tw[2 * m] : __ldg(&tw[2 * m]);
   if constexpr (EXACT && sizeof(C) == 8) {
-    const C l = __ldg(&tw[2 * m + 1]);
+    const C l = TWS ? tw[2 * m + 1] : __ldg(&tw[2 * m + 1]);
     if constexpr (DIR < 0) {
       const float lr = v.x * l.x - v.y * l.y, li = v.x * l.y + v.y * l.x;
       return mk(fmaf(v.x, w.x, fmaf(-v.y, w.y, lr)), fmaf(v.x, w.y, fmaf(v.y, w.x, li)));
@@ -326,7 +332,7 @@ __host__ __device__ constexpr int reg_elems(int N, int ncol) {
 }
 __host__ __device__ constexpr int reg_threads(int N, int ncol) { return N * ncol / reg_elems(N, ncol); }
 
-template <typename C, int N, int NCOL, int NT, int E, int DIR, bool EXACT, int R, int NS>
+template <typename C, int N, int NCOL, int NT, int E, int DIR, bool EXACT, int R, int NS, bool TWS>
 __device__ __forceinline__ void regs_pass(C (&v)[E], const C* __restrict__ tw) {
   constexpr int I = E / R;
   const int tid = threadIdx.x;
@@ -336,7 +342,7 @@ __device__ __forceinline__ void regs_pass(C (&v)[E], const C* __restrict__ tw) {
     if constexpr (NS > 1) {
       const int k = j % NS;
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[i * R + r] = twiddle_mul<DIR, EXACT>(v[i * R + r], tw, (k * r) * (N / (NS * R)));
+      for (int r = 1; r < R; ++r) v[i * R + r] = twiddle_mul<DIR, EXACT, TWS>(v[i * R + r], tw, (k * r) * (N / (NS * R)));
     }
     dft<R, DIR, EXACT>(&v[i * R]);
   }
@@ -367,6 +373,14 @@ __device__ __forceinline__ void smem_to_regs(C (&v)[E], const C* buf) {
   }
 }
 
+// True when the plan for N lists the same radices in reverse order.
+__host__ __device__ constexpr bool plan_palindrome(int N) {
+  const RadixPlan p = radix_plan(N);
+  for (int i = 0; i < p.npass; ++i)
+    if (p.r[i] != p.r[p.npass - 1 - i]) return false;
+  return true;
+}
+
 // Radix of pass p of the plan for N, taken in reverse order when REV is set.
 template <int N, bool REV>
 __host__ __device__ constexpr int plan_radix(int p) {
@@ -378,18 +392,19 @@ __host__ __device__ constexpr int plan_radix(int p) {
 // radices are taken in reverse order: a transform whose inputs are the outputs
 // of a forward-order transform (positions j + r N/R_last) then starts without an
 // exchange, since its first radix is that transform's last one.
-template <typename C, int N, int NCOL, int NT, int E, int DIR, bool EXACT, int PASS, int NS, bool REV = false>
+template <typename C, int N, int NCOL, int NT, int E, int DIR, bool EXACT, int PASS, int NS, bool REV = false,
+          bool TWS = false>
 __device__ __forceinline__ void regs_fft(C (&v)[E], C* buf, const C* __restrict__ tw) {
   constexpr int NP = radix_plan(N).npass;
   constexpr int R = plan_radix<N, REV>(PASS);
-  regs_pass<C, N, NCOL, NT, E, DIR, EXACT, R, NS>(v, tw);
+  regs_pass<C, N, NCOL, NT, E, DIR, EXACT, R, NS, TWS>(v, tw);
   if constexpr (PASS + 1 < NP) {
     constexpr int R2 = plan_radix<N, REV>(PASS + 1);
     regs_to_smem<C, N, NCOL, NT, E, R, NS>(v, buf);
     __syncthreads();
     smem_to_regs<C, N, NCOL, NT, E, R2>(v, buf);
     __syncthreads();
-    regs_fft<C, N, NCOL, NT, E, DIR, EXACT, PASS + 1, NS * R, REV>(v, buf, tw);
+    regs_fft<C, N, NCOL, NT, E, DIR, EXACT, PASS + 1, NS * R, REV, TWS>(v, buf, tw);
   }
 }
 

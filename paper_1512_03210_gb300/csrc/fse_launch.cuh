@@ -34,9 +34,10 @@ static cudaError_t col_launch(const ColArgs& a, const MulArgs& m, const void* tw
   static std::atomic<unsigned long long> done{0};
   cudaError_t e = allow_smem(k_colpass<Real, N, VAR>, smem, done);
   if (e != cudaSuccess) return e;
-  const int blocks = a.nplanes * a.tiles_per_plane;
+  const long long blocks = col_blocks(a, K::NCOL);
   if (blocks <= 0) return cudaSuccess;
-  k_colpass<Real, N, VAR><<<blocks, K::NT, smem, st>>>(a, m, reinterpret_cast<const C*>(tw));
+  if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_colpass<Real, N, VAR><<<(unsigned)blocks, K::NT, smem, st>>>(a, m, reinterpret_cast<const C*>(tw));
   return cudaGetLastError();
 }
 

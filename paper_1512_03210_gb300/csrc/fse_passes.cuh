@@ -50,7 +50,17 @@ struct ColArgs {
   int nplanes, ncols;      // planes; columns (lines) per plane, contiguous
   int n_load, n_store;     // rows loaded (rest zero) and rows stored
   int tiles_per_plane;
+  // > 0: tiles_per_plane full tiles cover the first tiles_per_plane * NCOL
+  // columns of every plane, and further tiles each take NCOL consecutive
+  // (plane, column) pairs of the `tail` remaining columns
+  int tail;
 };
+
+// Blocks of a column pass: the full tiles and the gathered tail tiles.
+__host__ __device__ inline long long col_blocks(const ColArgs& a, int ncol) {
+  const long long full = (long long)a.nplanes * a.tiles_per_plane;
+  return full + (a.tail > 0 ? ((long long)a.nplanes * a.tail + ncol - 1) / ncol : 0);
+}
 
 struct MulArgs {
   int mode;
@@ -130,9 +140,19 @@ struct ColCfg {
   static constexpr int MINB = (sizeof(C) == 8 && E > 16) ? (512 / NT > 0 ? 512 / NT : 1) : minb_for(NT, sizeof(C));
   // exchange tile, then (kernel-transform variant) the block's C^ values on |p| = 0..N/2
   static constexpr size_t TILE_BYTES = sizeof(C) * (size_t)N * (NCOL + 1);
-  static constexpr size_t tile_bytes() { return TILE_BYTES; }
-  static constexpr size_t chat_bytes() { return sizeof(Real) * (size_t)(N / 2 + 1) * NCOL; }
-  static constexpr size_t smem_bytes(int var) { return tile_bytes() + (var == 5 ? chat_bytes() : 0); }
+  __host__ __device__ static constexpr size_t tile_bytes() { return TILE_BYTES; }
+  __host__ __device__ static constexpr size_t chat_bytes() { return sizeof(Real) * (size_t)(N / 2 + 1) * NCOL; }
+  // copy of the twiddle table (pairs, 2 N entries), after the tile and C^ values
+  static constexpr size_t TW_BYTES = sizeof(C) * (size_t)(2 * N);
+  __host__ __device__ static constexpr int fit(size_t b) { return (int)((228u * 1024u) / (b + 1024u)); }
+  __host__ __device__ static constexpr size_t base_bytes(int var) { return tile_bytes() + (var == 5 ? chat_bytes() : 0); }
+  // the kernel-transform variant reads its table from shared memory when that
+  // costs no resident tile (measured faster there, slower in the other variants)
+  __host__ __device__ static constexpr bool tws(int var) {
+    return var == 5 &&
+           fit(base_bytes(var) + TW_BYTES) >= (fit(base_bytes(var)) < MINB ? fit(base_bytes(var)) : MINB);
+  }
+  __host__ __device__ static constexpr size_t smem_bytes(int var) { return base_bytes(var) + (tws(var) ? TW_BYTES : 0); }
 };
 
 template <typename Real, int N, int VAR>
@@ -141,10 +161,12 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
   typedef ColCfg<Real, N> K;
   typedef typename K::C C;
   constexpr int NCOL = K::NCOL, NT = K::NT, E = K::E, R0 = K::R0, RL = K::RL;
-  // forward . multiplier . inverse variants run the inverse with the radices
-  // reversed, so it starts on the forward's outputs as they sit in registers;
-  // the final outputs are then at positions j + r N/R0
-  constexpr bool FUSED = (VAR == COL_KIN || VAR == COL_KHAT);
+  // forward . multiplier . inverse variants whose radix plan reads the same
+  // reversed (all radix 8, e.g. N = 512) run the inverse straight on the
+  // forward's outputs as they sit in registers (positions j + r N/RL); other
+  // plans go through one exchange, which measured faster than reordering the
+  // inverse's radices
+  constexpr bool FUSED = (VAR == COL_KIN || VAR == COL_KHAT) && plan_palindrome(N);
   constexpr int RF = FUSED ? R0 : RL;
   // input r of the first pass (output r of the last) lies at rows >= N/2 for
   // every j when 2 r >= R: zero in a zero-padded input, dropped by the crop
@@ -155,65 +177,125 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int tid = threadIdx.x;
-  const int tp = bid / a.tiles_per_plane;
-  const int c0 = (bid - tp * a.tiles_per_plane) * NCOL;
+  static_assert(NT % NCOL == 0, "a thread keeps one column of the tile");
+  const int cme = tid % NCOL;  // this thread's column of the tile
+  // only passes over R2C bins (ncols = nx + 1) have tail tiles; they come
+  // first in the grid, so that they overlap the full tiles
+  constexpr bool TAILS = (VAR == COL_PADF || VAR == COL_CROPI || VAR == COL_KHAT);
+  const int ngat = TAILS && a.tail > 0 ? (a.nplanes * a.tail + NCOL - 1) / NCOL : 0;
+  const bool gather = bid < ngat;
+  const int breg = bid - ngat;
+  const int tp = gather ? 0 : breg / a.tiles_per_plane;
+  const int c0 = gather ? 0 : (breg - tp * a.tiles_per_plane) * NCOL;
   // kernel-transform pass over a full even set of planes: planes p and lp - p
   // (same |p|, same C^ values) run next to each other, so the octant is read
   // from HBM about once
   const int plane = (VAR == COL_KHAT && m.lp == a.nplanes && (m.lp & 1) == 0 && tp > 0)
                         ? ((tp & 1) ? (tp + 1) >> 1 : m.lp - (tp >> 1))
                         : tp;
-  C* base = reinterpret_cast<C*>(a.data) + (long long)plane * a.plane_stride + c0;
-  const int ncv = min(NCOL, a.ncols - c0);
+  // column cc of the tile -> (plane, x index); false past the data
+  auto col_of = [&](int cc, int& pl, int& px) -> bool {
+    if (!gather) {
+      pl = plane;
+      px = c0 + cc;
+      return px < a.ncols;
+    }
+    const int q = bid * NCOL + cc;
+    pl = q / a.tail;
+    px = a.tiles_per_plane * NCOL + q % a.tail;
+    if (pl < a.nplanes) return true;
+    pl = 0;
+    px = 0;
+    return false;
+  };
+  int my_plane = plane, my_px = c0 + cme;
+  bool my_ok = my_px < a.ncols;
+  if (gather) my_ok = col_of(cme, my_plane, my_px);
+  // row r of this thread's column is colp[r * line_stride + cme]
+  C* colp = reinterpret_cast<C*>(a.data) + (long long)my_plane * a.plane_stride + (my_px - cme);
   C v[E];
   Real* sC = reinterpret_cast<Real*>(smem_raw + K::TILE_BYTES);
+  constexpr bool TWS = K::tws(VAR);
+  if constexpr (TWS) {
+    // twiddle table to shared memory (its own cp.async group, waited for
+    // before the first exchange)
+    static_assert(K::base_bytes(VAR) % 16 == 0, "16-byte aligned table copy");
+    C* tws = reinterpret_cast<C*>(smem_raw + K::base_bytes(VAR));
+    constexpr int Q = (int)(2 * N * sizeof(C) / 16);
+    for (int q = tid; q < Q; q += NT)
+      cp_async<16>(reinterpret_cast<char*>(tws) + 16 * q, reinterpret_cast<const char*>(tw) + 16 * q);
+    cp_async_commit();
+    tw = tws;
+  }
   if constexpr (VAR == COL_KHAT) {
     // start fetching C^ (|p_row| = 0..N/2, this tile's columns) while the forward transform runs
     const Real* ch = reinterpret_cast<const Real*>(m.chat);
-    const int ap = m.lp ? abs(wrap_index(plane, m.lp)) : 0;
-    for (int idx = tid; idx < (N / 2 + 1) * NCOL; idx += NT) {
-      const int ar = idx / NCOL, c = idx % NCOL, px = c0 + c;
-      if (c < ncv && px <= (m.lx >> 1))
-        cp_async<sizeof(Real)>(&sC[idx], &ch[(long long)ar * m.chat_sr + (long long)ap * m.chat_sp + px]);
-      else
-        sC[idx] = Real(0);
+    if (!gather) {
+      const Real* chp = ch + (m.lp ? (long long)abs(wrap_index(plane, m.lp)) * m.chat_sp : 0) + c0;
+      for (int idx = tid; idx < (N / 2 + 1) * NCOL; idx += NT) {
+        const int ar = idx / NCOL, cc = idx % NCOL;
+        if (c0 + cc < a.ncols && c0 + cc <= (m.lx >> 1))
+          cp_async<sizeof(Real)>(&sC[idx], &chp[(long long)ar * m.chat_sr + cc]);
+        else
+          sC[idx] = Real(0);
+      }
+    } else {
+      for (int idx = tid; idx < (N / 2 + 1) * NCOL; idx += NT) {
+        const int ar = idx / NCOL, cc = idx % NCOL;
+        int pl, px;
+        const bool ok = col_of(cc, pl, px);
+        const int ap = m.lp ? abs(wrap_index(pl, m.lp)) : 0;
+        if (ok && px <= (m.lx >> 1))
+          cp_async<sizeof(Real)>(&sC[idx], &ch[(long long)ar * m.chat_sr + (long long)ap * m.chat_sp + px]);
+        else
+          sC[idx] = Real(0);
+      }
     }
+    cp_async_commit();
   }
 
   // inputs of the first pass straight from global memory
 #pragma unroll
   for (int i = 0; i < E / R0; ++i) {
-    const int w = tid + i * NT, c = w % NCOL, j = w / NCOL;
+    const int j = (tid + i * NT) / NCOL;
 #pragma unroll
     for (int r = 0; r < R0; ++r) {
       const int row = j + r * (N / R0);
       if (HALF_IN && 2 * r >= R0) {
         v[i * R0 + r] = mk(Real(0), Real(0));  // rows >= N/2 of a zero-padded line
       } else {
-        v[i * R0 + r] = (row < a.n_load && c < ncv) ? base[(long long)row * a.line_stride + c] : mk(Real(0), Real(0));
+        v[i * R0 + r] = (row < a.n_load && my_ok) ? colp[(long long)row * a.line_stride + cme] : mk(Real(0), Real(0));
       }
     }
   }
+  if constexpr (TWS) {
+    // the twiddle group has landed (the C^ group may still be in flight); the
+    // first exchange's barrier publishes the table to the block
+    if constexpr (VAR == COL_KHAT) cp_async_wait_group<1>();
+    else cp_async_wait_group<0>();
+    if constexpr (radix_plan(N).npass < 2) __syncthreads();
+  }
   if constexpr (VAR == COL_FWD || VAR == COL_INV || VAR == COL_PADF || VAR == COL_CROPI) {
-    regs_fft<C, N, NCOL, NT, E, DIR1, EXACT, 0, 1>(v, buf, tw);
+    regs_fft<C, N, NCOL, NT, E, DIR1, EXACT, 0, 1, false, TWS>(v, buf, tw);
   } else {
-    regs_fft<C, N, NCOL, NT, E, -1, EXACT, 0, 1>(v, buf, tw);
+    regs_fft<C, N, NCOL, NT, E, -1, EXACT, 0, 1, false, TWS>(v, buf, tw);
     // spectral multiplier on the outputs (row = frequency index along the axis)
     if constexpr (VAR == COL_KIN) {
       // kinetic phase exp(-i f theta_k) from the plan's octant table, indexed by
       // |p_x| (column), |p_plane| and |p_row| (row = frequency index along the axis)
-      const C* tab = reinterpret_cast<const C*>(m.kin) + (m.lp ? (long long)abs(wrap_index(plane, m.lp)) * m.kin_sp : 0);
+      const C* tab = reinterpret_cast<const C*>(m.kin) + (m.lp ? (long long)abs(wrap_index(my_plane, m.lp)) * m.kin_sp : 0);
       const Real sc = Real(m.scale);
+      const int ax = abs(wrap_index(min(my_px, m.lx - 1), m.lx));
 #pragma unroll
       for (int i = 0; i < E / RL; ++i) {
-        const int w = tid + i * NT, c = w % NCOL, j = w / NCOL;
-        const int ax = abs(wrap_index(min(c0 + c, m.lx - 1), m.lx));
+        const int j = (tid + i * NT) / NCOL;
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
           const int row = j + r * (N / RL);
-          const C t = c < ncv ? __ldg(&tab[(long long)abs(wrap_index(row, m.lr)) * m.kin_sr + ax]) : mk(Real(1), Real(0));
+          const C t = my_ok ? __ldg(&tab[(long long)abs(wrap_index(row, m.lr)) * m.kin_sr + ax]) : mk(Real(1), Real(0));
           const C x = unit_mul(v[i * RL + r], t.x, t.y, m.conj != 0);
-          v[i * RL + r] = mk(sc * x.x, sc * x.y);
+          if constexpr (FUSED) v[i * RL + r] = mk(sc * x.x, sc * x.y);
+          else buf[row * (NCOL + 1) + cme] = mk(sc * x.x, sc * x.y);
         }
       }
     } else {
@@ -221,23 +303,22 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
       // the column (x, an R2C bin 0..nx) and plane factors are fixed per thread
       cp_async_wait_all();
       __syncthreads();
-      const Real kp = m.lp ? Real(m.dkp) * Real(wrap_index(plane, m.lp)) : Real(0);
-      const Real kpo = (m.lp && 2 * plane == m.lp) ? Real(0) : kp;
+      const Real kp = m.lp ? Real(m.dkp) * Real(wrap_index(my_plane, m.lp)) : Real(0);
+      const Real kpo = (m.lp && 2 * my_plane == m.lp) ? Real(0) : kp;
       const bool ddi = m.mode == MUL_DDI;
+      const Real kx = Real(m.dkx) * Real(my_px);
+      const Real kxo = (2 * my_px == m.lx) ? Real(0) : kx;
+      // q(k) = A + B kr + q2 kr^2 (kr replaced by 0 in B at the Nyquist row)
+      const Real Aq = Real(m.q[0]) * kx * kx + Real(m.q[1]) * kp * kp + Real(m.q[3]) * kxo * kpo;
+      const Real Bq = Real(m.q[4]) * kxo + Real(m.q[5]) * kpo;
 #pragma unroll
       for (int i = 0; i < E / RL; ++i) {
-        const int w = tid + i * NT, c = w % NCOL, j = w / NCOL;
-        const int px = c0 + c;
-        const Real kx = Real(m.dkx) * Real(px);
-        const Real kxo = (2 * px == m.lx) ? Real(0) : kx;
-        // q(k) = A + B kr + q2 kr^2 (kr replaced by 0 in B at the Nyquist row)
-        const Real Aq = Real(m.q[0]) * kx * kx + Real(m.q[1]) * kp * kp + Real(m.q[3]) * kxo * kpo;
-        const Real Bq = Real(m.q[4]) * kxo + Real(m.q[5]) * kpo;
+        const int j = (tid + i * NT) / NCOL;
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
           const int row = j + r * (N / RL);
           const int pr = wrap_index(row, m.lr);
-          const Real cv = sC[abs(pr) * NCOL + c];
+          const Real cv = sC[abs(pr) * NCOL + cme];
           Real f;
           if (ddi) {
             const Real kr = Real(m.dkr) * Real(pr);
@@ -248,22 +329,28 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
             f = Real(m.a0) * cv;
           }
           const C x = v[i * RL + r];
-          v[i * RL + r] = mk(f * x.x, f * x.y);
+          if constexpr (FUSED) v[i * RL + r] = mk(f * x.x, f * x.y);
+          else buf[row * (NCOL + 1) + cme] = mk(f * x.x, f * x.y);
         }
       }
     }
-    // the last exchange of the forward transform ended with a barrier, so buf is free
-    regs_fft<C, N, NCOL, NT, E, +1, EXACT, 0, 1, true>(v, buf, tw);
+    if constexpr (!FUSED) {
+      // (the forward's last exchange ended with a barrier, so buf was free)
+      __syncthreads();
+      smem_to_regs<C, N, NCOL, NT, E, R0>(v, buf);
+      __syncthreads();
+    }
+    regs_fft<C, N, NCOL, NT, E, +1, EXACT, 0, 1, FUSED, TWS>(v, buf, tw);
   }
   // outputs of the last pass to global memory (rows >= n_store cropped)
 #pragma unroll
   for (int i = 0; i < E / RF; ++i) {
-    const int w = tid + i * NT, c = w % NCOL, j = w / NCOL;
+    const int j = (tid + i * NT) / NCOL;
 #pragma unroll
     for (int r = 0; r < RF; ++r) {
       const int row = j + r * (N / RF);
       if (HALF_OUT && 2 * r >= RF) continue;  // rows >= N/2 are cropped
-      if (row < a.n_store && c < ncv) base[(long long)row * a.line_stride + c] = v[i * RF + r];
+      if (row < a.n_store && my_ok) colp[(long long)row * a.line_stride + cme] = v[i * RF + r];
     }
   }
 }
@@ -289,14 +376,28 @@ struct XCfg {
   static constexpr int LDS2 = NCOL / 2 + 1;
   static constexpr int TOT = NCOL * NX;
   static constexpr int PER = (TOT + NT - 1) / NT;
-  static constexpr size_t smem_bytes() {
+  static constexpr int MINB = sizeof(Real) == 4 ? 4 : 2;
+  __host__ __device__ static constexpr size_t smem_bytes() {
     return sizeof(C) * (size_t)((NX * LDS) > (2 * NX * LDS2) ? (NX * LDS) : (2 * NX * LDS2));
   }
-  static constexpr int MINB = sizeof(Real) == 4 ? 4 : 2;
 };
 
-__device__ __forceinline__ long long srow(int l, int ny, int mul) {
-  return (long long)(l / ny) * (mul * ny) + (l % ny);
+// Line l0 + q of a tile -> its (y, z) indices, from y0 = l0 % ny and
+// z0 = l0 / ny (one division per tile rather than one per element).
+__device__ __forceinline__ void line_yz(int y0, int z0, int q, int ny, int& y, int& z) {
+  y = y0 + q;
+  z = z0;
+  while (y >= ny) {
+    y -= ny;
+    ++z;
+  }
+}
+
+// Row of S holding the x-half-spectrum of line l0 + q (S rows: mul * ny per z).
+__device__ __forceinline__ long long srow(int y0, int z0, int q, int ny, int mul) {
+  int y, z;
+  line_yz(y0, z0, q, ny, y, z);
+  return (long long)z * (mul * ny) + y;
 }
 
 // Real values of the NCOL lines of a tile (one per (line, x) item of the
@@ -327,15 +428,21 @@ __device__ __forceinline__ void r2c_rows(const XArgs& a, typename Cplx<Real>::T*
   }
   __syncthreads();
   fft_tile<C, 2 * NX, NCOL / 2, NT, -1, false>(buf, tw2n);
-  for (int idx = tid; idx < (NCOL / 2) * (NX + 1); idx += NT) {
-    const int q = idx / (NX + 1), k = idx % (NX + 1);
-    const C zk = buf[k * LDS2 + q];
-    const C zm = buf[((2 * NX - k) % (2 * NX)) * LDS2 + q];
-    const int la = l0 + 2 * q;
-    const C A = mk(Real(0.5) * (zk.x + zm.x), Real(0.5) * (zk.y - zm.y));
-    const C B = mk(Real(0.5) * (zk.y + zm.y), Real(0.5) * (zm.x - zk.x));
-    if (la < a.nlines) S[srow(la, a.ny, a.srow_mul) * a.sx + k] = A;
-    if (la + 1 < a.nlines) S[srow(la + 1, a.ny, a.srow_mul) * a.sx + k] = B;
+  const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
+  constexpr int NH = (NCOL / 2) * (NX + 1), PH = (NH + NT - 1) / NT;
+#pragma unroll
+  for (int it = 0; it < PH; ++it) {
+    const int idx = tid + it * NT;
+    if (idx < NH) {
+      const int q = idx / (NX + 1), k = idx % (NX + 1);
+      const C zk = buf[k * LDS2 + q];
+      const C zm = buf[((2 * NX - k) % (2 * NX)) * LDS2 + q];
+      const int la = l0 + 2 * q;
+      const C A = mk(Real(0.5) * (zk.x + zm.x), Real(0.5) * (zk.y - zm.y));
+      const C B = mk(Real(0.5) * (zk.y + zm.y), Real(0.5) * (zm.x - zk.x));
+      if (la < a.nlines) S[srow(y0, z0, 2 * q, a.ny, a.srow_mul) * a.sx + k] = A;
+      if (la + 1 < a.nlines) S[srow(y0, z0, 2 * q + 1, a.ny, a.srow_mul) * a.sx + k] = B;
+    }
   }
 }
 
@@ -352,6 +459,7 @@ __device__ __forceinline__ void c2r_rows(const XArgs& a, typename Cplx<Real>::T*
   constexpr int NCOL = K::NCOL, NT = K::NT, LDS2 = K::LDS2, TOT = K::TOT, PER = K::PER;
   const int tid = threadIdx.x;
   const C* S = reinterpret_cast<const C*>(a.spec);
+  const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
   constexpr int NH = (NCOL / 2) * (NX + 1), PH = (NH + NT - 1) / NT;
 #pragma unroll
   for (int it = 0; it < PH; ++it) {
@@ -360,8 +468,8 @@ __device__ __forceinline__ void c2r_rows(const XArgs& a, typename Cplx<Real>::T*
       const int q = idx / (NX + 1), k = idx % (NX + 1);
       const int la = l0 + 2 * q;
       C A = mk(Real(0), Real(0)), B = A;
-      if (la < a.nlines) A = S[srow(la, a.ny, a.srow_mul) * a.sx + k];
-      if (la + 1 < a.nlines) B = S[srow(la + 1, a.ny, a.srow_mul) * a.sx + k];
+      if (la < a.nlines) A = S[srow(y0, z0, 2 * q, a.ny, a.srow_mul) * a.sx + k];
+      if (la + 1 < a.nlines) B = S[srow(y0, z0, 2 * q + 1, a.ny, a.srow_mul) * a.sx + k];
       buf[k * LDS2 + q] = mk(A.x - B.y, A.y + B.x);
       if (k > 0 && k < NX) buf[(2 * NX - k) * LDS2 + q] = mk(A.x + B.y, B.x - A.y);
     }
@@ -396,10 +504,10 @@ __device__ __forceinline__ void phase_sincos(float th, float* sn, float* cs) {
 __device__ __forceinline__ void phase_sincos(double th, double* sn, double* cs) { sincos(th, sn, cs); }
 
 template <typename Real>
-__device__ __forceinline__ Real trap_phase(const XArgs& a, int x, int lg) {
+__device__ __forceinline__ Real trap_phase(const XArgs& a, int x, int y, int z) {
   const Real X = Real(a.lo0) + Real(a.h0) * Real(x);
-  const Real Y = Real(a.lo1) + Real(a.h1) * Real(lg % a.ny);
-  const Real Z = Real(a.lo2) + Real(a.h2) * Real(lg / a.ny);
+  const Real Y = Real(a.lo1) + Real(a.h1) * Real(y);
+  const Real Z = Real(a.lo2) + Real(a.h2) * Real(z);
   return Real(a.pa) * X * X + Real(a.pb) * Y * Y + Real(a.pc) * X * Y + Real(a.pe) * Z * Z;
 }
 
@@ -414,6 +522,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int tid = threadIdx.x;
   const int l0 = bid * NCOL;
+  const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;  // (y, z) of the tile's first line
   C* psi = reinterpret_cast<C*>(a.psi);
 
   if constexpr (KIND == XP_FWD || KIND == XP_INV || KIND == XP_E) {
@@ -475,17 +584,19 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
         const int l = idx / NX, x = idx % NX;
         const int lg = l0 + l;
         if (lg < a.nlines) {
+          int yl, zl;
+          line_yz(y0, z0, l, a.ny, yl, zl);
           const long long o = (long long)lg * NX + x;
           const C u = u1p[o];
           const C g = psi[o];
-          const Real th = Real(a.beta_dt) * (u.x * u.x + u.y * u.y) + Real(a.lam) * vphi[it] + trap_phase<Real>(a, x, lg);
+          const Real th = Real(a.beta_dt) * (u.x * u.x + u.y * u.y) + Real(a.lam) * vphi[it] + trap_phase<Real>(a, x, yl, zl);
           Real sn, cs;
           sincos(th, &sn, &cs);
           const C u2 = mk(u.x * cs + u.y * sn, u.y * cs - u.x * sn);
           const Real r = g.x * u2.y - g.y * u2.x;
           rr[it] = r;
           psi[o] = mk(g.x * cs - g.y * sn, g.y * cs + g.x * sn);
-          const double X = a.lo0 + a.h0 * x, Y = a.lo1 + a.h1 * (lg % a.ny), Z = a.lo2 + a.h2 * (lg / a.ny);
+          const double X = a.lo0 + a.h0 * x, Y = a.lo1 + a.h1 * yl, Z = a.lo2 + a.h2 * zl;
           dg0 += (double)r * (a.dp[0] * X * X + a.dp[1] * Y * Y + a.dp[2] * X * Y + a.dp[3] * Z * Z);
           dg1 += (double)r * (a.dp[4] * X * X + a.dp[5] * Y * Y + a.dp[6] * X * Y + a.dp[7] * Z * Z);
           dg2 += (double)r * (a.dp[8] * X * X + a.dp[9] * Y * Y + a.dp[10] * X * Y + a.dp[11] * Z * Z);
@@ -565,9 +676,11 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
           const int lg = l0 + l;
           C u2 = mk(Real(0), Real(0));
           if (lg < a.nlines) {
+            int yl, zl;
+            line_yz(y0, z0, l, a.ny, yl, zl);
             const C u = psi[(long long)lg * NX + x];
             const Real rho = u.x * u.x + u.y * u.y;
-            const Real th = Real(a.beta_dt) * rho + Real(a.lam) * vphi[it] + trap_phase<Real>(a, x, lg);
+            const Real th = Real(a.beta_dt) * rho + Real(a.lam) * vphi[it] + trap_phase<Real>(a, x, yl, zl);
             Real sn, cs;
             phase_sincos(th, &sn, &cs);
             u2 = unit_mul(u, cs, -sn, false);

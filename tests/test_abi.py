@@ -52,7 +52,14 @@ def test_plan_validation_on_host():
     assert _create(dict(good, kernel="ddi3d"))[0] == 1           # the DDI kernel needs dim 3
     assert _create(dict(good, n=(100, 128)))[0] == 2             # 100 is not 2^a or 3*2^a
     assert _create(dict(good, n=(1024, 1024)))[0] == 2           # above the largest size
-    assert _create(dict(good, mu=0.5))[0] == 2
+    # Coulomb-type exponent: 0 < mu <= dim - 1 (Eq. Kernel); the DDI kernel uses mu = 1
+    assert _create(dict(good, mu=0.5))[0] == 0
+    assert _create(dict(good, mu=0.0))[0] == 1
+    assert _create(dict(good, mu=1.5))[0] == 1
+    d3 = I.workload("3d_dipolar_128")
+    assert _create(dict(d3, kernel="coulomb", mu=2.0))[0] == 0
+    assert _create(dict(d3, kernel="coulomb", mu=2.5))[0] == 1
+    assert _create(dict(d3, mu=0.5))[0] == 1
 
 
 def test_null_arguments_rejected():

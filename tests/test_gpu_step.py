@@ -75,6 +75,26 @@ def test_3d_f64_matches_oracle(lib, kernel):
     assert _rel(got, ref) < 2e-12
 
 
+@pytest.mark.parametrize("dim,mu", [(2, 0.5), (3, 0.5), (3, 1.5), (3, 2.0)])
+def test_coulomb_mu_f64_matches_oracle(lib, dim, mu):
+    """Coulomb-type kernel 1/|x|^mu, 0 < mu <= d - 1 (Eq. Kernel): nodes, near field, C^."""
+    d = _case2d(mu=mu) if dim == 2 else _case3d(kernel="coulomb", mu=mu)
+    p = O.params(d)
+    psi0 = _gauss(p)
+    ref = O.evolve(psi0, p, 0.2, 2)
+    got, _ = _run_gpu(lib, d, psi0, 0.2, 2)
+    assert _rel(got, ref) < 2e-12
+
+
+def test_coulomb_mu_f32_matches_oracle(lib):
+    d = _case3d(kernel="coulomb", mu=1.5, prec="f32")
+    p = O.params(d)
+    psi0 = _gauss(p)
+    ref = O.evolve(psi0, p, 0.2, 3)
+    got, _ = _run_gpu(lib, d, psi0, 0.2, 3)
+    assert _rel(got, ref) < 5e-6 * 3
+
+
 @pytest.mark.parametrize("n", [8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512])
 def test_every_fft_length_2d_f64(lib, n):
     """Each supported n (FFT lengths n and 2n) on a square 2D grid, one full step."""
