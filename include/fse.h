@@ -46,7 +46,7 @@ typedef enum {
   FSE_ERR_NONFINITE = 6     /* a reduction met NaN or Inf */
 } fse_status;
 
-typedef enum { FSE_KERNEL_NONE = 0, FSE_KERNEL_COULOMB = 1, FSE_KERNEL_DDI3D = 2 } fse_kernel;
+typedef enum { FSE_KERNEL_NONE = 0, FSE_KERNEL_COULOMB = 1, FSE_KERNEL_DDI3D = 2, FSE_KERNEL_DDI2D = 3 } fse_kernel;
 typedef enum { FSE_F32 = 0, FSE_F64 = 1 } fse_prec;
 
 /*
@@ -58,10 +58,13 @@ typedef enum { FSE_F32 = 0, FSE_F64 = 1 } fse_prec;
  *   beta       local cubic interaction strength
  *   lambda     nonlocal interaction strength
  *   dt         time step (may be negative: the scheme is time-reversible)
- *   kernel     fse_kernel: none, Coulomb-type 1/(2^{d-1} pi |x|^mu), or 3D DDI
+ *   kernel     fse_kernel: none, Coulomb-type 1/(2^{d-1} pi |x|^mu), 3D DDI
+ *              (-1 + 3 (n.k)^2/|k|^2) or 2D DDI (3 [(n_perp.k)^2 - n3^2 |k|^2] /
+ *              (2|k|)), Eq. Kernel
  *   mu         exponent of the Coulomb-type kernel, 0 < mu <= dim - 1 (Eq.
- *              Kernel); the 3D DDI kernel is built on mu = 1
- *   dip_n[3]   dipole axis n (unit vector) for FSE_KERNEL_DDI3D
+ *              Kernel); the DDI kernels are built on mu = 1
+ *   dip_n[3]   dipole axis n (unit vector) for FSE_KERNEL_DDI3D and
+ *              FSE_KERNEL_DDI2D (2D: n_perp = (n1, n2) in the plane, n3 normal)
  *   gamma[3]   harmonic trap frequencies (Eq. harm_poten)
  *   gs_delta, gs_h, gs_tmin  Gaussian-sum fit (Eq. GS-Gene): near-field
  *              radius in unit-box units, sinc-quadrature step and lower
@@ -70,6 +73,11 @@ typedef enum { FSE_F32 = 0, FSE_F64 = 1 } fse_prec;
  *   renormalize  0: the paper's scheme; 1: after each step rescale psi so that
  *              its float64 mass equals the mass at the start of the fse_step
  *              call (holds the float32 mass drift; not part of the paper)
+ *   order      time-splitting order: 0 or 2 = TS2-GauSum (Strang, Eqs.
+ *              tssp1-tssp3); 4 = symmetric composition of three TS2-GauSum
+ *              sub-steps of lengths w1 dt, w0 dt, w1 dt with w1 = 1/(2 - 2^{1/3})
+ *              and w0 = 1 - 2 w1 (the higher-order extension of Section 4.2;
+ *              not available to fse_step_adjoint and the batch calls)
  */
 typedef struct {
   int dim;
@@ -83,6 +91,7 @@ typedef struct {
   double gs_delta, gs_h, gs_tmin;
   int prec;
   int renormalize;
+  int order;
 } fse_params;
 
 /* Observables (Eqs. mass, energy, AME, CoM, ConWidth) at time t, in float64.
@@ -98,7 +107,7 @@ typedef struct {
  * *workspace_bytes the size of the device workspace the caller must supply.
  * Errors: FSE_ERR_INVALID (null pointers, dim, s <= 0, box, dt = 0, kernel
  * and dim mismatch, mu outside (0, dim - 1] for the Coulomb-type kernel or
- * mu != 1 for the DDI kernel), FSE_ERR_UNSUPPORTED (a size outside the
+ * mu != 1 for a DDI kernel, order not 0, 2 or 4), FSE_ERR_UNSUPPORTED (a size outside the
  * supported set). On error *out is NULL. */
 fse_status fse_plan_create(const fse_params* params, void* cuda_stream, fse_plan_t* out,
                            size_t* workspace_bytes);
@@ -138,7 +147,7 @@ fse_status fse_step_host(fse_plan_t plan, void* psi_host, double t0, int nsteps,
  * synchronises the stream). The paper has no adjoint: this is the transpose
  * of the real-linearised map of Eqs. tssp1-tssp3. Errors: FSE_ERR_INVALID
  * (null or misaligned buffers, precompute not run), FSE_ERR_UNSUPPORTED
- * (a plan with renormalize = 1). Uses the workspace's scratch wave function
+ * (a plan with renormalize = 1 or order 4). Uses the workspace's scratch wave function
  * and spectrum, so it must not overlap other calls on the same plan. */
 fse_status fse_step_adjoint(fse_plan_t plan, const void* psi_n, void* g, double t_n,
                             const double* gamma_n, double* dgamma_n);
@@ -194,7 +203,7 @@ fse_status fse_plan_profile_read(fse_plan_t plan, double* ms, long long* count);
  * with its own grid size, s, m, Omega, beta, lambda, dt and trap) advanced
  * together: runs of equal grid size share one launch per pass and one kernel
  * transform; a run advanced in a batch is bit-identical to the same run
- * advanced alone with fse_step. Requirements: dim 2, FSE_F32, renormalize 0,
+ * advanced alone with fse_step. Requirements: dim 2, FSE_F32, renormalize 0, order 2,
  * one box and one kernel (none or Coulomb) for the whole batch. */
 typedef struct fse_batch* fse_batch_t;
 

@@ -37,6 +37,14 @@ Readings where the paper is silent or ambiguous (each pinned by a test):
    Nyquist index; forward DFT unnormalised, inverse 1/N.
 6. The grid is n points per axis, x_l = lo + l h, l = 0..n-1 (the printed
    index set duplicates the periodic endpoint). m = 0 unless given.
+7. Coulomb-type kernels 1/|x|^mu, 0 < mu <= d - 1 (Eq. Kernel): the same
+   sinc quadrature with exponent mu, lower end t_min = -36/mu by default.
+8. Order 4 (``order=4``): the symmetric triple jump of three TS2-GauSum
+   sub-steps, the higher-order extension that Section 4.2 mentions.
+9. 2D DDI (``kernel="ddi2d"``): Eq. Kernel_Rot prints only
+   -3/2 L~_2 (1/(2 pi|x|)); the rotation-invariant term -3/2 (-n_3^2 Lap) of
+   Eq. Kernel and of the Section 2 reformulation is kept, integrated over the
+   window: K^ = 3/2 (k^T M_perp k - n_3^2 (tb-ta) |k|^2) C^.
 
 The time-integrated trap P (Eq. int_poten) and dipole matrix
 M = int m m^T dtau (Eq. Kernel_Rot / solu_step2_conv) are computed here by
@@ -53,6 +61,7 @@ __all__ = [
     "kinetic_step", "rotation", "trap_potential", "trap_integral", "dipole_axis",
     "dipole_integral", "gausum_nodes", "gausum_g_table", "near_field",
     "gausum_octant", "gausum_multiplier", "kernel_multiplier", "kernel_multiplier_instant",
+    "split_step4", "TRIPLE_JUMP_W1", "TRIPLE_JUMP_W0",
     "pad", "crop", "nonlocal_potential", "potential_step", "split_step", "evolve",
     "observables", "com_velocity_spectral", "mass",
     "adjoint_split_step", "evolve_with_states", "objective_overlap", "gradient_adjoint",
@@ -64,7 +73,7 @@ class Params:
 
     FIELDS = dict(dim=2, n=None, lo=None, hi=None, s=1.0, m=0.0, omega=0.0, beta=0.0,
                   lam=0.0, dt=1e-3, kernel="coulomb", mu=1.0, dip_n=(0.0, 0.0, 1.0),
-                  gamma=(1.0, 1.0, 1.0), gs_delta=1e-3, gs_h=0.125, gs_tmin=None)
+                  gamma=(1.0, 1.0, 1.0), gs_delta=1e-3, gs_h=0.125, gs_tmin=None, order=2)
 
     def __init__(self, **kw):
         for k, v in self.FIELDS.items():
@@ -78,8 +87,12 @@ class Params:
             raise ValueError("the 3D dipolar kernel needs dim=3")
         if self.kernel == "ddi3d" and self.mu != 1.0:
             raise ValueError("the 3D dipolar kernel is built on 1/|x| (mu = 1)")
+        if self.kernel == "ddi2d" and (self.dim != 2 or self.mu != 1.0):
+            raise ValueError("the 2D dipolar kernel needs dim=2 and is built on 1/(2 pi |x|)")
         if self.kernel == "coulomb" and not (0.0 < self.mu <= self.dim - 1):
             raise ValueError("Coulomb-type kernel 1/|x|^mu needs 0 < mu <= d - 1 (Eq. Kernel)")
+        if self.order not in (2, 4):
+            raise ValueError("splitting order 2 (Strang, Eqs. tssp1-tssp3) or 4 (triple jump)")
         if not self.gs_tmin:
             # lower end of the sinc quadrature: the dropped tail is ~ e^{mu t_min} / mu
             self.gs_tmin = -36.0 / self.mu
@@ -320,23 +333,30 @@ def gausum_multiplier(p, octant=None):
     return oc[np.ix_(*reversed(idx))]
 
 
-def _quad_form(p, M, Chat):
-    """3 (k^T M k) C^ with odd factors zeroed at the Nyquist index (reading 5)."""
+def _quad_form(p, M, Chat, factor=3.0):
+    """factor (k^T M k) C^ over the grid's axes, odd factors zeroed at the Nyquist index (reading 5)."""
     k = wavenumbers(p, padded=True)
     ko = wavenumbers(p, padded=True, odd=True)
     q = 0.0
-    for i in range(3):
+    for i in range(p.dim):
         q = q + M[i, i] * k[i] * k[i]
-        for j in range(i + 1, 3):
+        for j in range(i + 1, p.dim):
             q = q + 2 * M[i, j] * ko[i] * ko[j]
-    return 3.0 * q * Chat
+    return factor * q * Chat
+
+
+def _ksq(p):
+    k = wavenumbers(p, padded=True)
+    return sum(k[j] * k[j] for j in range(p.dim))
 
 
 def kernel_multiplier(p, ta, tb, Chat=None):
     """Transform of the time-integrated kernel K~ over [ta, tb] (Eq. solu_step2_conv).
 
     Coulomb: (tb-ta) C^.  3D DDI: -(tb-ta) + 3 k^T M k C^ with M the integral
-    of m m^T (the operator L~_3 applied to 1/(4 pi|x|)).
+    of m m^T (the operator L~_3 applied to 1/(4 pi|x|)).  2D DDI:
+    3/2 (k^T M_perp k - n_3^2 (tb-ta) |k|^2) C^ with C^ the transform of
+    1/(2 pi|x|) and M_perp the in-plane block of M (Eq. Kernel, 2D DDI row).
     """
     p = params(p)
     C = gausum_multiplier(p) if Chat is None else Chat
@@ -344,6 +364,11 @@ def kernel_multiplier(p, ta, tb, Chat=None):
         return (tb - ta) * C
     if p.kernel == "ddi3d":
         return -(tb - ta) + _quad_form(p, dipole_integral(p, ta, tb), C)
+    if p.kernel == "ddi2d":
+        # -3/2 L~_2 (1/(2 pi|x|)) plus the rotation-invariant -3/2 (-n_3^2 Lap) part
+        # of Eq. Kernel, integrated over the window (reading 9)
+        n3 = float(p.dip_n[2])
+        return _quad_form(p, dipole_integral(p, ta, tb), C, 1.5) - 1.5 * n3 * n3 * (tb - ta) * _ksq(p) * C
     return np.zeros_like(C)
 
 
@@ -356,6 +381,10 @@ def kernel_multiplier_instant(p, t, Chat=None):
     if p.kernel == "ddi3d":
         m = dipole_axis(p, t)
         return -1.0 + _quad_form(p, np.outer(m, m), C)
+    if p.kernel == "ddi2d":
+        m = dipole_axis(p, t)
+        n3 = float(p.dip_n[2])
+        return _quad_form(p, np.outer(m, m), C, 1.5) - 1.5 * n3 * n3 * _ksq(p) * C
     return np.zeros_like(C)
 
 
@@ -399,13 +428,36 @@ def split_step(phi, p, tn, gamma=None, Chat=None):
     return kinetic_step(u2, p, 0.5 * p.dt)
 
 
+# Fourth-order symmetric composition of three Strang steps ("triple jump",
+# Yoshida 1990): S4(dt) = S2(w1 dt) S2(w0 dt) S2(w1 dt) with w1 = 1/(2 - 2^{1/3})
+# and w0 = 1 - 2 w1 < 0 (the middle sub-step runs backwards in time). This is
+# the extension of TS2-GauSum to higher-order splitting that Section 4.2 notes.
+TRIPLE_JUMP_W1 = 1.0 / (2.0 - 2.0 ** (1.0 / 3.0))
+TRIPLE_JUMP_W0 = 1.0 - 2.0 * TRIPLE_JUMP_W1
+
+
+def split_step4(phi, p, tn, gamma=None, Chat=None):
+    """One fourth-order step from t_n to t_n + dt: three TS2-GauSum sub-steps
+    of lengths w1 dt, w0 dt, w1 dt over consecutive windows."""
+    p = params(p)
+    t = tn
+    for w in (TRIPLE_JUMP_W1, TRIPLE_JUMP_W0, TRIPLE_JUMP_W1):
+        tau = w * p.dt
+        u1 = kinetic_step(phi, p, 0.5 * tau)
+        u2 = potential_step(u1, p, t, t + tau, gamma, Chat)
+        phi = kinetic_step(u2, p, 0.5 * tau)
+        t = t + tau
+    return phi
+
+
 def evolve(phi, p, t0, nsteps, gammas=None, Chat=None):
-    """nsteps TS2-GauSum steps; gammas (optional) is [nsteps][dim] per-step trap frequencies."""
+    """nsteps steps of order p.order; gammas (optional) is [nsteps][dim] per-step trap frequencies."""
     p = params(p)
     if Chat is None and p.kernel != "none":
         Chat = gausum_multiplier(p)
+    step = split_step4 if p.order == 4 else split_step
     for n in range(nsteps):
-        phi = split_step(phi, p, t0 + n * p.dt, None if gammas is None else gammas[n], Chat)
+        phi = step(phi, p, t0 + n * p.dt, None if gammas is None else gammas[n], Chat)
     return phi
 
 

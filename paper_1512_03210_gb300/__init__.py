@@ -32,7 +32,7 @@ ROOT = os.path.dirname(HERE)
 HEADER = os.path.join(ROOT, "include", "fse.h")
 
 FSE_OK = 0
-KERNELS = {"none": 0, "coulomb": 1, "ddi3d": 2}
+KERNELS = {"none": 0, "coulomb": 1, "ddi3d": 2, "ddi2d": 3}
 PRECS = {"f32": 0, "f64": 1}
 PASS_KINDS = ["xfwd", "xinv", "E", "A", "col", "kin", "pad", "khat", "pre", "other"]
 
@@ -44,6 +44,7 @@ class FseParams(ct.Structure):
         ("lambda_", ct.c_double), ("dt", ct.c_double), ("kernel", ct.c_int), ("mu", ct.c_double),
         ("dip_n", ct.c_double * 3), ("gamma", ct.c_double * 3), ("gs_delta", ct.c_double),
         ("gs_h", ct.c_double), ("gs_tmin", ct.c_double), ("prec", ct.c_int), ("renormalize", ct.c_int),
+        ("order", ct.c_int),
     ]
 
 
@@ -165,6 +166,7 @@ def to_params(p: dict) -> FseParams:
     fp.gs_tmin = float(p.get("gs_tmin", 0.0))
     fp.prec = PRECS[p.get("prec", "f32")]
     fp.renormalize = int(p.get("renormalize", 0))
+    fp.order = int(p.get("order", 2))
     return fp
 
 

@@ -52,6 +52,7 @@ extern "C" fse_status fse_step_adjoint(fse_plan_t P, const void* psi_n, void* g,
   if (!P || !psi_n || !g) return FSE_ERR_INVALID;
   if (!P->ws || !P->precomputed) return fail(P, FSE_ERR_INVALID, "fse_kernel_precompute has not run");
   if (P->p.renormalize) return fail(P, FSE_ERR_UNSUPPORTED, "adjoint of a renormalised plan");
+  if (P->p.order != 2) return fail(P, FSE_ERR_UNSUPPORTED, "adjoint of the fourth-order composition");
   if (reinterpret_cast<uintptr_t>(g) % P->csize != 0 || reinterpret_cast<uintptr_t>(psi_n) % P->csize != 0)
     return fail(P, FSE_ERR_INVALID, "misaligned buffer");
   const double dt = P->p.dt, ta = t_n, tb = t_n + dt;

@@ -37,6 +37,10 @@ namespace {
 
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
+// Weights of the fourth-order triple jump (Yoshida 1990): w1 = 1/(2 - 2^{1/3}), w0 = 1 - 2 w1.
+const double kTripleW1 = 1.0 / (2.0 - std::cbrt(2.0));
+const double kTripleW0 = 1.0 - 2.0 * kTripleW1;
+
 bool size_supported(int n) {
   static const int ok[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512};
   for (int v : ok)
@@ -269,6 +273,9 @@ XArgs x_args(fse_plan* P, void* psi, void* spec) {
 // Kinetic sub-step of factor f (1: dt/2 as in Eqs. tssp1/tssp3; 2: two merged halves)
 // on a field already transformed along x: fwd-y, fwd-z . phase . inv-z, inv-y
 // (3D) or fwd-y . phase . inv-y (2D). On exit the field is x-spectral.
+// f selects the plan's kinetic table: 1 the half step (dt/2; w1 dt/2 at order
+// 4), 2 two merged half steps (dt; w1 dt), 3 the middle of the fourth-order
+// composition ((w1 + w0) dt / 2); -1 the conjugate half step (adjoint).
 fse_status kinetic_yz(fse_plan* P, void* psi, double f, double dt) {
   (void)dt;  // the phase tables were built with the plan's dt
   MulArgs m;
@@ -278,8 +285,10 @@ fse_status kinetic_yz(fse_plan* P, void* psi, double f, double dt) {
     m.kin = P->ws_ptr(P->off_kin_half);
   } else if (f == 2.0) {
     m.kin = P->ws_ptr(P->off_kin_full);
+  } else if (f == 3.0 && P->p.order == 4) {
+    m.kin = P->ws_ptr(P->off_kin_mid);
   } else {
-    return fail(P, FSE_ERR_INVALID, "kinetic factor must be 1, 2 or -1");
+    return fail(P, FSE_ERR_INVALID, "kinetic table selector must be 1, 2, 3 (order 4) or -1");
   }
   m.conj = f < 0.0;
   m.lx = P->nx;
@@ -311,7 +320,18 @@ fse_status nonlocal_yz(fse_plan* P, void* spec, double ta, double tb, bool integ
   MulArgs m;
   std::memset(&m, 0, sizeof(m));
   const double d = integrated ? (tb - ta) : 1.0;
-  m.mode = P->p.kernel == FSE_KERNEL_DDI3D ? MUL_DDI : MUL_COULOMB;
+  const bool ddi = P->p.kernel == FSE_KERNEL_DDI3D || P->p.kernel == FSE_KERNEL_DDI2D;
+  m.mode = ddi ? MUL_DDI : MUL_COULOMB;
+  // M = int m m^T over the window (or m m^T of the axis mdir at one time)
+  double M[6] = {0, 0, 0, 0, 0, 0};
+  if (ddi) {
+    if (integrated) {
+      dipole_matrix(P, ta, tb, M);
+    } else {
+      M[0] = mdir[0] * mdir[0]; M[1] = mdir[1] * mdir[1]; M[2] = mdir[2] * mdir[2];
+      M[3] = mdir[0] * mdir[1]; M[4] = mdir[0] * mdir[2]; M[5] = mdir[1] * mdir[2];
+    }
+  }
   m.lx = 2 * P->nx;
   m.dkx = 2 * kPi / (2.0 * (P->p.hi[0] - P->p.lo[0]));
   m.chat = P->ws_ptr(P->off_chat);
@@ -325,7 +345,17 @@ fse_status nonlocal_yz(fse_plan* P, void* spec, double ta, double tb, bool integ
     m.chat_sp = 0;
     m.chat_sr = P->nx + 1;
     m.scale = extra_scale / (4.0 * P->nx * P->ny);
-    m.a0 = d * m.scale;
+    if (m.mode == MUL_COULOMB) {
+      m.a0 = d * m.scale;
+    } else {
+      // 2D DDI: 3/2 (k^T M_perp k - n_3^2 d |k|^2) C^ (Eq. Kernel, 2D DDI row, with the
+      // rotation-invariant n_3 term kept); columns carry k_x, rows k_y
+      const double n3 = P->p.dip_n[2], c = 1.5 * m.scale;
+      m.a0 = 0.0;
+      m.q[0] = c * (M[0] - n3 * n3 * d);
+      m.q[2] = c * (M[1] - n3 * n3 * d);
+      m.q[4] = 2 * c * M[3];
+    }
     ColArgs a{spec, 0, P->sx, 1, P->nx + 1, P->ny, P->ny, tiles(P, 2 * P->ny, P->nx + 1)};
     return col(P, FSE_PASS_KHAT, 2 * P->ny, COL_KHAT, a, m);
   }
@@ -340,13 +370,6 @@ fse_status nonlocal_yz(fse_plan* P, void* spec, double ta, double tb, bool integ
   if (m.mode == MUL_COULOMB) {
     m.a0 = d * m.scale;
   } else {
-    double M[6];
-    if (integrated) {
-      dipole_matrix(P, ta, tb, M);
-    } else {
-      M[0] = mdir[0] * mdir[0]; M[1] = mdir[1] * mdir[1]; M[2] = mdir[2] * mdir[2];
-      M[3] = mdir[0] * mdir[1]; M[4] = mdir[0] * mdir[2]; M[5] = mdir[1] * mdir[2];
-    }
     m.a0 = -d * m.scale;
     const double c = 3.0 * m.scale;
     m.q[0] = c * M[0];
@@ -379,10 +402,18 @@ fse_status run_steps(fse_plan* P, void* psi, double t0, int nsteps, const double
   if (rn) xe.part = renorm_part(P);
   const int ncx = P->prec == FSE_F32 ? xpass_ncol<float>(P->nx) : xpass_ncol<double>(P->nx);
   const int xblocks = (xa.nlines + ncx - 1) / ncx;
+  // sub-steps of one step: TS2-GauSum itself, or the fourth-order triple jump
+  // w1, w0, w1; the kinetic half steps between sub-steps and between steps merge
+  const int nsub = P->p.order == 4 ? 3 : 1;
+  const double wsub[3] = {nsub == 3 ? kTripleW1 : 1.0, kTripleW0, kTripleW1};
   if ((st = xpass(P, XP_FWD, xa)) != FSE_OK) return st;
-  for (int n = 0; n < nsteps; ++n) {
-    const double ta = t0 + n * dt, tb = ta + dt;
-    if ((st = kinetic_yz(P, psi, n == 0 ? 1.0 : 2.0, dt)) != FSE_OK) return st;
+  for (int n = 0; n < nsteps * nsub; ++n) {
+    const int step = n / nsub, sub = n % nsub;
+    double ta = t0 + step * dt;
+    for (int i = 0; i < sub; ++i) ta += wsub[i] * dt;
+    const double tb = sub == nsub - 1 ? t0 + (step + 1) * dt : ta + wsub[sub] * dt;
+    const double kf = n == 0 ? 1.0 : (sub == 0 ? 2.0 : 3.0);
+    if ((st = kinetic_yz(P, psi, kf, dt)) != FSE_OK) return st;
     if (nl) {
       if ((st = xpass(P, XP_E, xe)) != FSE_OK) return st;
       if ((st = nonlocal_yz(P, spec, ta, tb, true, nullptr, 1.0)) != FSE_OK) return st;
@@ -391,7 +422,7 @@ fse_status run_steps(fse_plan* P, void* psi, double t0, int nsteps, const double
     }
     if (rn && (st = renorm_step(P, xblocks)) != FSE_OK) return st;
     double pc[4];
-    trap_coefficients(P, ta, tb, gps ? gps + (size_t)n * P->dim : nullptr, pc);
+    trap_coefficients(P, ta, tb, gps ? gps + (size_t)step * P->dim : nullptr, pc);
     XArgs xA = xa;
     xA.beta_dt = P->p.beta * (tb - ta);
     xA.lam = P->p.lambda;
@@ -437,8 +468,9 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
   const fse_params& p = *prm;
   if (p.dim != 2 && p.dim != 3) return FSE_ERR_INVALID;
   if (!(p.s > 0.0) || !(p.m >= 0.0) || p.dt == 0.0 || !std::isfinite(p.dt)) return FSE_ERR_INVALID;
-  if (p.kernel < FSE_KERNEL_NONE || p.kernel > FSE_KERNEL_DDI3D) return FSE_ERR_INVALID;
+  if (p.kernel < FSE_KERNEL_NONE || p.kernel > FSE_KERNEL_DDI2D) return FSE_ERR_INVALID;
   if (p.kernel == FSE_KERNEL_DDI3D && p.dim != 3) return FSE_ERR_INVALID;
+  if (p.kernel == FSE_KERNEL_DDI2D && (p.dim != 2 || p.mu != 1.0)) return FSE_ERR_INVALID;
   if (p.prec != FSE_F32 && p.prec != FSE_F64) return FSE_ERR_INVALID;
   for (int j = 0; j < p.dim; ++j) {
     if (!(p.hi[j] > p.lo[j])) return FSE_ERR_INVALID;
@@ -447,12 +479,14 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
   if (p.kernel == FSE_KERNEL_COULOMB && !(p.mu > 0.0 && p.mu <= p.dim - 1)) return FSE_ERR_INVALID;
   if (p.kernel == FSE_KERNEL_DDI3D && p.mu != 1.0) return FSE_ERR_INVALID;
   if (p.renormalize != 0 && p.renormalize != 1) return FSE_ERR_INVALID;
+  if (p.order != 0 && p.order != 2 && p.order != 4) return FSE_ERR_INVALID;
   fse_plan* P = new (std::nothrow) fse_plan();
   if (!P) return FSE_ERR_NOMEM;
   P->p = p;
   if (P->p.gs_delta <= 0) P->p.gs_delta = 1e-3;
   if (P->p.gs_h <= 0) P->p.gs_h = 0.125;
   if (P->p.kernel == FSE_KERNEL_NONE) P->p.mu = 1.0;
+  if (P->p.order == 0) P->p.order = 2;
   // the dropped tail of the sinc quadrature is ~ e^{mu t_min} / mu
   if (P->p.gs_tmin == 0) P->p.gs_tmin = -36.0 / P->p.mu;
   P->stream = reinterpret_cast<cudaStream_t>(stream);
@@ -521,6 +555,12 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
   off = align256(off + kin_elems * P->csize);
   P->off_kin_full = off;
   off = align256(off + kin_elems * P->csize);
+  if (P->p.order == 4) {
+    P->off_kin_mid = off;
+    off = align256(off + kin_elems * P->csize);
+    P->off_kin_mid2 = off;
+    off = align256(off + kin_elems * P->csize);
+  }
   P->off_spec = off;
   const size_t spec_rows = (size_t)(p.dim == 3 ? P->nz * 2 * P->ny : P->ny);
   const size_t spec_bytes = spec_rows * P->sx * P->csize;
@@ -581,14 +621,21 @@ fse_status fse_kernel_precompute(fse_plan_t P) {
   {
     const double dk[3] = {2 * kPi / (P->p.hi[0] - P->p.lo[0]), 2 * kPi / (P->p.hi[1] - P->p.lo[1]),
                           P->dim == 3 ? 2 * kPi / (P->p.hi[2] - P->p.lo[2]) : 0.0};
-    void* kh = P->ws_ptr(P->off_kin_half);
-    void* kf = P->ws_ptr(P->off_kin_full);
-    e = P->prec == FSE_F32
-            ? launch_kin_table<float>(kh, kf, P->nx, P->ny, P->nz, dk[0], dk[1], dk[2], P->p.s, P->p.m * P->p.m,
-                                      P->p.dt, P->stream)
-            : launch_kin_table<double>(kh, kf, P->nx, P->ny, P->nz, dk[0], dk[1], dk[2], P->p.s, P->p.m * P->p.m,
-                                       P->p.dt, P->stream);
-    if (launched(P, e, "kinetic tables") != FSE_OK) return FSE_ERR_CUDA;
+    // (half, full) tables of a step length L: phases L/4 and L/2 times (|k|^2+m^2)^s.
+    // Order 2: L = dt. Order 4: L = w1 dt (first/last half step, merged w1 dt
+    // between steps), then L = (w1 + w0) dt for the middle half steps.
+    const int nt = P->p.order == 4 ? 2 : 1;
+    for (int it = 0; it < nt; ++it) {
+      const double L = P->p.order == 4 ? (it == 0 ? kTripleW1 : kTripleW1 + kTripleW0) * P->p.dt : P->p.dt;
+      void* kh = P->ws_ptr(it == 0 ? P->off_kin_half : P->off_kin_mid);
+      void* kf = P->ws_ptr(it == 0 ? P->off_kin_full : P->off_kin_mid2);
+      e = P->prec == FSE_F32
+              ? launch_kin_table<float>(kh, kf, P->nx, P->ny, P->nz, dk[0], dk[1], dk[2], P->p.s, P->p.m * P->p.m,
+                                        L, P->stream)
+              : launch_kin_table<double>(kh, kf, P->nx, P->ny, P->nz, dk[0], dk[1], dk[2], P->p.s, P->p.m * P->p.m,
+                                         L, P->stream);
+      if (launched(P, e, "kinetic tables") != FSE_OK) return FSE_ERR_CUDA;
+    }
   }
   if (P->p.kernel != FSE_KERNEL_NONE) {
     char* base = reinterpret_cast<char*>(P->ws_ptr(P->off_spec));

@@ -177,8 +177,9 @@ fse_status fse_batch_create(const fse_params* runs, int nruns, void* stream, fse
   *workspace_bytes = 0;
   for (int r = 0; r < nruns; ++r) {
     const fse_params& p = runs[r];
-    if (p.dim != 2 || p.prec != FSE_F32 || p.renormalize != 0) return FSE_ERR_UNSUPPORTED;
-    if (p.kernel == FSE_KERNEL_DDI3D) return FSE_ERR_INVALID;
+    if (p.dim != 2 || p.prec != FSE_F32 || p.renormalize != 0 || (p.order != 0 && p.order != 2))
+      return FSE_ERR_UNSUPPORTED;
+    if (p.kernel == FSE_KERNEL_DDI3D || p.kernel == FSE_KERNEL_DDI2D) return FSE_ERR_INVALID;
     if (p.lo[0] != runs[0].lo[0] || p.lo[1] != runs[0].lo[1] || p.hi[0] != runs[0].hi[0] ||
         p.hi[1] != runs[0].hi[1] || p.kernel != runs[0].kernel)
       return FSE_ERR_UNSUPPORTED;  // one box and one kernel per batch

@@ -26,6 +26,9 @@ struct fse_plan {
   std::vector<int> tw_len;
   std::vector<size_t> tw_off;
   size_t off_chat = 0, off_spec = 0, off_stage = 0, off_tmp = 0, off_red = 0, off_kin_half = 0, off_kin_full = 0;
+  // fourth-order composition: kinetic table of the (w1 + w0) dt / 2 sub-step
+  // between sub-steps (and the unused full-step output of its build)
+  size_t off_kin_mid = 0, off_kin_mid2 = 0;
   size_t pre_w = 0, pre_tau = 0, pre_gl = 0, pre_g[3] = {0, 0, 0}, pre_cs = 0, pre_y = 0, pre_yw = 0;
   size_t ws_bytes = 0, psi_bytes = 0;
 

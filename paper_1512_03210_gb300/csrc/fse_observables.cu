@@ -261,7 +261,7 @@ fse_status observables(fse_plan* P, const void* psi_in, double t, const double* 
     if ((st = xpass(P, XP_FWD, xa)) != FSE_OK) return st;
     if ((st = xpass(P, XP_E, xa)) != FSE_OK) return st;  // tmp = nx psi, S = R2C of nx^2 rho
     double mdir[3] = {0, 0, 0};
-    if (P->p.kernel == FSE_KERNEL_DDI3D) {
+    if (P->p.kernel == FSE_KERNEL_DDI3D || P->p.kernel == FSE_KERNEL_DDI2D) {
       // m(t) = A(t)^T n
       const double n1 = P->p.dip_n[0], n2 = P->p.dip_n[1], n3 = P->p.dip_n[2];
       mdir[0] = o.c * n1 - o.s * n2;

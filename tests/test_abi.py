@@ -60,6 +60,13 @@ def test_plan_validation_on_host():
     assert _create(dict(d3, kernel="coulomb", mu=2.0))[0] == 0
     assert _create(dict(d3, kernel="coulomb", mu=2.5))[0] == 1
     assert _create(dict(d3, mu=0.5))[0] == 1
+    # the 2D DDI kernel needs dim 2 and mu = 1
+    assert _create(dict(good, kernel="ddi2d"))[0] == 0
+    assert _create(dict(good, kernel="ddi2d", mu=0.5))[0] == 1
+    assert _create(dict(d3, kernel="ddi2d"))[0] == 1
+    # splitting order: 2 (TS2-GauSum) or 4 (triple jump)
+    assert _create(dict(good, order=4))[0] == 0
+    assert _create(dict(good, order=3))[0] == 1
 
 
 def test_null_arguments_rejected():

@@ -86,6 +86,52 @@ def test_coulomb_mu_f64_matches_oracle(lib, dim, mu):
     assert _rel(got, ref) < 2e-12
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fourth_order_f64_matches_oracle(lib, dim):
+    """Triple-jump composition of TS2-GauSum sub-steps (w1 dt, w0 dt, w1 dt), 3 steps."""
+    d = _case2d(order=4) if dim == 2 else _case3d(order=4)
+    p = O.params(d)
+    psi0 = _gauss(p)
+    ref = O.evolve(psi0, p, 0.15, 3)
+    got, _ = _run_gpu(lib, d, psi0, 0.15, 3)
+    assert _rel(got, ref) < 5e-12
+
+
+def test_fourth_order_f32_and_reversible(lib):
+    d = _case3d(order=4, prec="f32")
+    p = O.params(d)
+    psi0 = _gauss(p)
+    ref = O.evolve(psi0, p, 0.15, 2)
+    got, _ = _run_gpu(lib, d, psi0, 0.15, 2)
+    assert _rel(got, ref) < 5e-6 * 3 * 2
+    d64 = _case2d(order=4)
+    fw, _ = _run_gpu(lib, d64, _gauss(O.params(d64)), 0.1, 2)
+    back, _ = _run_gpu(lib, dict(d64, dt=-d64["dt"]), fw, 0.1 + 2 * d64["dt"], 2)
+    assert _rel(back, _gauss(O.params(d64))) < 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 2e-12), ("f32", 5e-6)])
+def test_ddi_2d_matches_oracle(lib, prec, tol):
+    """2D DDI (Eq. Kernel): 3/2 (k^T M_perp k - n3^2 dt |k|^2) C^ with the rotating axis."""
+    d = _case2d(kernel="ddi2d", dip_n=(0.48, -0.36, 0.8), lam=25.0, prec=prec)
+    p = O.params(d)
+    psi0 = _gauss(p)
+    ref = O.evolve(psi0, p, 0.1, 3)
+    got, _ = _run_gpu(lib, d, psi0, 0.1, 3)
+    assert _rel(got, ref) < tol * 3
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_kinetic_mass_term_f64_matches_oracle(lib, dim):
+    """(-Lap + m^2)^s with m > 0 (Eq. SFSE)."""
+    d = _case2d(m=0.9) if dim == 2 else _case3d(m=0.6)
+    p = O.params(d)
+    psi0 = _gauss(p)
+    ref = O.evolve(psi0, p, 0.0, 2)
+    got, _ = _run_gpu(lib, d, psi0, 0.0, 2)
+    assert _rel(got, ref) < 2e-12
+
+
 def test_coulomb_mu_f32_matches_oracle(lib):
     d = _case3d(kernel="coulomb", mu=1.5, prec="f32")
     p = O.params(d)

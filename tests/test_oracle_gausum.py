@@ -316,3 +316,41 @@ def test_kernel_exponent_range():
     assert O.Params(dim=2, mu=0.5, **base).gs_tmin == -72.0
     with pytest.raises(ValueError):
         O.Params(dim=3, n=(8,) * 3, lo=(-1.0,) * 3, hi=(1.0,) * 3, kernel="ddi3d", mu=0.5)
+
+
+def test_ddi_2d_gaussian_closed_form():
+    """2D DDI (Eq. Kernel): Phi = -3/2 (d_{n_perp n_perp} - n_3^2 Lap) f with
+    f = (1/(2 pi|x|)) * rho = e^{-r^2/2} I0(r^2/2) / (2 sqrt(pi)) for rho = e^{-r^2}/pi."""
+    nvec = np.array([0.48, -0.36, 0.8])
+    p = O.Params(dim=2, n=(64, 64), lo=(-8.0, -8.0), hi=(8.0, 8.0), kernel="ddi2d", dip_n=tuple(nvec))
+    X = O.coords(p)
+    r2 = X[0] ** 2 + X[1] ** 2
+    rho = np.exp(-r2) / math.pi
+    Phi = O.nonlocal_potential(rho, p, O.kernel_multiplier_instant(p, 0.0))
+    u = r2 / 2
+    r = np.sqrt(r2)
+    c = 1.0 / (2 * math.sqrt(math.pi))
+    g1 = special.i1e(u) - special.i0e(u)                                  # G'(u), G = e^{-u} I0(u)
+    i1_over_u = np.where(u > 1e-12, special.i1e(u) / np.where(u > 0, u, 1.0), 0.5)
+    g2 = 2 * special.i0e(u) - 2 * special.i1e(u) - i1_over_u              # G''(u)
+    f1_over_r = c * g1                                                    # f'(r)/r
+    f2 = c * (g2 * r2 + g1)                                               # f''(r)
+    npp = nvec[:2]
+    nx = np.where(r > 0, (npp[0] * X[0] + npp[1] * X[1]) / np.where(r > 0, r, 1.0), 0.0)
+    dnn = nx ** 2 * f2 + (npp @ npp - nx ** 2) * f1_over_r                # d_{n_perp n_perp} f
+    lap = f2 + f1_over_r
+    ex = -1.5 * (dnn - nvec[2] ** 2 * lap)
+    assert np.max(np.abs(Phi - ex)) < 1e-12 * np.max(np.abs(ex))
+
+
+def test_ddi_2d_integrated_kernel_matches_instant_quadrature():
+    """K^ over [ta, tb] is the time integral of the instantaneous multiplier (Eq. Kernel_Rot)."""
+    p = O.Params(dim=2, n=(8, 8), lo=(-2.0, -2.0), hi=(2.0, 2.0), kernel="ddi2d", omega=1.3,
+                 dip_n=(0.6, 0.0, 0.8))
+    C = O.gausum_multiplier(p)
+    ta, tb = 0.2, 0.9
+    got = O.kernel_multiplier(p, ta, tb, C)
+    tq, wq = np.polynomial.legendre.leggauss(24)
+    t = 0.5 * (tb - ta) * tq + 0.5 * (ta + tb)
+    ref = sum(0.5 * (tb - ta) * w * O.kernel_multiplier_instant(p, tt, C) for tt, w in zip(t, wq))
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))

@@ -21,10 +21,11 @@ def _p(**kw):
     return O.Params(**base)
 
 
-def test_kinetic_step_is_the_tssp1_sum():
-    """Eq. tssp1 written as explicit sums over p, q with W_pq(x_l, y_m)."""
+@pytest.mark.parametrize("m", [0.0, 0.8])
+def test_kinetic_step_is_the_tssp1_sum(m):
+    """Eq. tssp1 written as explicit sums over p, q with W_pq(x_l, y_m), mass m of (-Lap + m^2)^s."""
     L, M = 6, 8
-    p = _p(n=(L, M), lo=(-1.0, -2.0), hi=(2.0, 1.5), s=0.65, dt=0.37)
+    p = _p(n=(L, M), lo=(-1.0, -2.0), hi=(2.0, 1.5), s=0.65, dt=0.37, m=m)
     rng = np.random.default_rng(1)
     phi = rng.standard_normal((M, L)) + 1j * rng.standard_normal((M, L))
     hx = (p.hi[0] - p.lo[0]) / L
@@ -226,3 +227,66 @@ def test_angular_momentum_conserved_isotropic_coulomb():
     q = O.Params(**dict(vars(p), gamma=(1.0, 1.5, 1.0)))
     l2 = O.observables(O.evolve(phi, q, 0.0, 200), q, 200 * p.dt)["lz"]
     assert abs(l2 - l0) > 1e-3
+
+
+# --- fourth-order composition (triple jump of TS2-GauSum sub-steps) -------------
+
+def test_triple_jump_weights():
+    """w1 = 1/(2 - 2^{1/3}), w0 = 1 - 2 w1: the weights sum to one and their cubes cancel."""
+    w1, w0 = O.TRIPLE_JUMP_W1, O.TRIPLE_JUMP_W0
+    assert abs(2 * w1 + w0 - 1.0) < 1e-15
+    assert abs(2 * w1 ** 3 + w0 ** 3) < 1e-14
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.7])
+def test_coherent_state_s1_fourth_order(omega):
+    """s=1 isotropic harmonic trap (exact coherent state): order 4 error ratio ~16."""
+    errs = []
+    for dt in (0.1, 0.05):
+        p = _p(n=(64, 64), lo=(-10.0, -10.0), hi=(10.0, 10.0), s=1.0, omega=omega,
+               dt=dt, gamma=(1.0, 1.0), order=4)
+        X = O.coords(p)
+        q0 = np.array([1.5, -0.5])
+        phi = _coherent(X, q0, np.zeros(2), 0.0, 2)
+        T = 1.0
+        out = O.evolve(phi, p, 0.0, int(round(T / dt)))
+        q = q0 * math.cos(T)
+        pm = -q0 * math.sin(T)
+        errs.append(np.max(np.abs(out - _coherent(X, q, pm, T, 2))))
+    assert errs[1] < 1e-5
+    assert 13.0 < errs[0] / errs[1] < 19.0
+
+
+def test_fourth_order_nonlinear_convergence():
+    """Fractional, rotating, anisotropic trap, cubic and Coulomb terms: errors
+    against a fine run shrink ~16x per halving of dt (order 2 shrinks ~4x)."""
+    base = dict(n=(32, 32), lo=(-6.0, -6.0), hi=(6.0, 6.0), s=0.8, omega=0.6, beta=20.0, lam=5.0,
+                kernel="coulomb", gamma=(1.0, 1.3))
+    X = O.coords(_p(**base))
+    phi0 = (np.pi ** -0.5 * np.exp(-((X[0] - 0.5) ** 2 + X[1] ** 2) / 2)).astype(complex)
+    T = 0.4
+    ref = O.evolve(phi0, _p(dt=T / 160, order=4, **base), 0.0, 160)
+    e4, e2 = [], []
+    for nst in (10, 20):
+        e4.append(np.max(np.abs(O.evolve(phi0, _p(dt=T / nst, order=4, **base), 0.0, nst) - ref)))
+        e2.append(np.max(np.abs(O.evolve(phi0, _p(dt=T / nst, order=2, **base), 0.0, nst) - ref)))
+    assert 12.0 < e4[0] / e4[1] < 20.0
+    assert 3.5 < e2[0] / e2[1] < 4.5
+    assert e4[1] < e2[1] / 10
+
+
+def test_fourth_order_reversible_and_free():
+    """Symmetric composition: stepping back with -dt restores the state; with
+    V = beta = lambda = 0 the step is the exact free propagator."""
+    base = dict(n=(24, 16), lo=(-5.0, -4.0), hi=(5.0, 4.0), s=0.7, omega=0.8, beta=30.0, lam=8.0,
+                kernel="coulomb", gamma=(1.0, 1.4), order=4)
+    X = O.coords(_p(**base))
+    phi = (np.exp(-((X[0] - 0.3) ** 2 + 1.3 * X[1] ** 2) / 2 + 0.4j * X[0])).astype(complex)
+    fw = O.evolve(phi, _p(dt=0.05, **base), 0.2, 3)
+    back = O.evolve(fw, _p(dt=-0.05, **base), 0.35, 3)
+    assert np.max(np.abs(back - phi)) < 1e-12 * np.max(np.abs(phi))
+    free = dict(base, beta=0.0, lam=0.0, kernel="none", gamma=(0.0, 0.0))
+    p = _p(dt=0.07, **free)
+    got = O.evolve(phi, p, 0.1, 1)
+    ex = np.fft.ifftn(np.exp(-0.5j * p.dt * O.kinetic_symbol(p)) * np.fft.fftn(phi))
+    assert np.max(np.abs(got - ex)) < 1e-13
