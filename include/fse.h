@@ -78,6 +78,13 @@ typedef enum { FSE_F32 = 0, FSE_F64 = 1 } fse_prec;
  *              sub-steps of lengths w1 dt, w0 dt, w1 dt with w1 = 1/(2 - 2^{1/3})
  *              and w0 = 1 - 2 w1 (the higher-order extension of Section 4.2;
  *              not available to fse_step_adjoint and the batch calls)
+ *   lat_amp, lat_k[3]  optical lattice added to the harmonic trap,
+ *              V += lat_amp sum_v sin^2(lat_k[v] x_v) in the lab frame (the
+ *              harmonic-plus-lattice potential of Section 3.3); 0 = none. Its
+ *              time integral over each step (Eq. int_poten) is taken by
+ *              Gauss-Legendre quadrature, as Section 4.2 prescribes for a
+ *              general V; not available to the batch calls
+ *   quad_nodes  Gauss-Legendre nodes of that quadrature, 1..16; 0 selects 8
  */
 typedef struct {
   int dim;
@@ -92,6 +99,9 @@ typedef struct {
   int prec;
   int renormalize;
   int order;
+  double lat_amp;
+  double lat_k[3];
+  int quad_nodes;
 } fse_params;
 
 /* Observables (Eqs. mass, energy, AME, CoM, ConWidth) at time t, in float64.
@@ -107,7 +117,8 @@ typedef struct {
  * *workspace_bytes the size of the device workspace the caller must supply.
  * Errors: FSE_ERR_INVALID (null pointers, dim, s <= 0, box, dt = 0, kernel
  * and dim mismatch, mu outside (0, dim - 1] for the Coulomb-type kernel or
- * mu != 1 for a DDI kernel, order not 0, 2 or 4), FSE_ERR_UNSUPPORTED (a size outside the
+ * mu != 1 for a DDI kernel, order not 0, 2 or 4, non-finite lattice
+ * parameters or quad_nodes outside 0..16), FSE_ERR_UNSUPPORTED (a size outside the
  * supported set). On error *out is NULL. */
 fse_status fse_plan_create(const fse_params* params, void* cuda_stream, fse_plan_t* out,
                            size_t* workspace_bytes);
@@ -203,7 +214,7 @@ fse_status fse_plan_profile_read(fse_plan_t plan, double* ms, long long* count);
  * with its own grid size, s, m, Omega, beta, lambda, dt and trap) advanced
  * together: runs of equal grid size share one launch per pass and one kernel
  * transform; a run advanced in a batch is bit-identical to the same run
- * advanced alone with fse_step. Requirements: dim 2, FSE_F32, renormalize 0, order 2,
+ * advanced alone with fse_step. Requirements: dim 2, FSE_F32, renormalize 0, order 2, no lattice,
  * one box and one kernel (none or Coulomb) for the whole batch. */
 typedef struct fse_batch* fse_batch_t;
 
@@ -230,6 +241,42 @@ fse_status fse_batch_destroy(fse_batch_t batch);
 const char* fse_batch_error(fse_batch_t batch);
 /* Kernel launches issued by the batch since creation. */
 long long fse_batch_launch_count(fse_batch_t batch);
+
+/* ---------------------------------------------------------------------------
+ * Ground state by GF-GauSum (Section 3.2, Eqs. gf-eq1 to gffg33): the
+ * gradient flow with discrete normalisation in the laboratory frame, each
+ * backward-Euler step (1/dt + (-Lap+m^2)^s/2 + V + beta|phi^n|^2 + lambda Phi^n
+ * - Omega L_z) phi^(1) = phi^n/dt solved by BiCGStab on the system left-
+ * preconditioned with P_Delta = [1/dt + (-Lap+m^2)^s/2]^-1 (Eq. precond_type1),
+ * then phi^{n+1} = phi^(1)/||phi^(1)||. It uses the plan's grid, s, m, Omega,
+ * beta, lambda, kernel (Phi = U * |phi^n|^2 with the un-rotated axis n), the
+ * trap gamma and the optical lattice; the plan's dt and order play no part.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  double dt;        /* gradient-flow time step (> 0) */
+  int max_outer;    /* at most this many normalised steps */
+  double tol;       /* stop once max |phi^{n+1} - phi^n| / dt <= tol */
+  int max_inner;    /* BiCGStab iterations per step, at most */
+  double inner_tol; /* BiCGStab stops at ||r|| <= inner_tol ||b|| */
+} fse_gs_opts;
+typedef struct {
+  int outer;        /* normalised steps taken */
+  int inner;        /* BiCGStab iterations, all steps */
+  double change;    /* max |phi^{n+1} - phi^n| / dt of the last step */
+  double residual;  /* ||r|| / ||b|| of the last inner solve */
+} fse_gs_info;
+/* Device workspace (bytes, 256-byte aligned) that fse_ground_state needs for
+ * its Krylov vectors on this plan: ten complex and three real fields. */
+fse_status fse_ground_state_workspace(fse_plan_t plan, size_t* bytes);
+/* psi (device, plan layout): initial guess on entry (scaled to unit mass),
+ * the last iterate on return. The call synchronises the plan's stream (the
+ * Krylov scalars are read on the host) and uses the plan's scratch field and
+ * spectrum. info (nullable) receives the counts. Errors: FSE_ERR_INVALID (null
+ * or misaligned buffers, precompute not run, dt <= 0, negative counts or
+ * tolerances, zero initial field), FSE_ERR_NOMEM (workspace too small),
+ * FSE_ERR_NONFINITE (the iteration produced a non-finite field). */
+fse_status fse_ground_state(fse_plan_t plan, void* psi, void* workspace, size_t workspace_bytes,
+                            const fse_gs_opts* opts, fse_gs_info* info);
 
 /* Largest npoints accepted by fse_mass_noalloc (4096 partials of 65536 points). */
 #define FSE_NOALLOC_MAX_POINTS (4096LL * 65536LL)

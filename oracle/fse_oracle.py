@@ -17,7 +17,10 @@ What it computes, in the paper's order (Antoine, Tang & Zhang, arXiv
   GS-Gene, FourSeriB3, tensor, taylor) with the DDI rewritten as Coulomb
   acting on a differentiated density (Section 2, end);
 * the observables of Section 1 and 4.1 (Eqs. mass, energy, AME, CoM,
-  ConWidth) and the spectral centre-of-mass law (Eq. PCoM2, Appendix B).
+  ConWidth) and the spectral centre-of-mass law (Eq. PCoM2, Appendix B);
+* the GF-GauSum ground-state iteration of Section 3.2 (backward-Euler
+  gradient flow with discrete normalisation, BiCGStab on the system
+  preconditioned by P_Delta, Eq. precond_type1).
 
 Readings where the paper is silent or ambiguous (each pinned by a test):
 
@@ -45,6 +48,9 @@ Readings where the paper is silent or ambiguous (each pinned by a test):
    -3/2 L~_2 (1/(2 pi|x|)); the rotation-invariant term -3/2 (-n_3^2 Lap) of
    Eq. Kernel and of the Section 2 reformulation is kept, integrated over the
    window: K^ = 3/2 (k^T M_perp k - n_3^2 (tb-ta) |k|^2) C^.
+10. A general V (Section 4.2: P by numerical quadrature): the harmonic trap
+   plus an optical lattice lat_amp sum_v sin^2(lat_k_v x_v) in the lab frame,
+   the potential of the harmonic-plus-lattice example of Section 3.3.
 
 The time-integrated trap P (Eq. int_poten) and dipole matrix
 M = int m m^T dtau (Eq. Kernel_Rot / solu_step2_conv) are computed here by
@@ -65,6 +71,8 @@ __all__ = [
     "pad", "crop", "nonlocal_potential", "potential_step", "split_step", "evolve",
     "observables", "com_velocity_spectral", "mass",
     "adjoint_split_step", "evolve_with_states", "objective_overlap", "gradient_adjoint",
+    "gf_lz", "gf_potential", "gf_precond", "gf_matvec", "bicgstab", "gf_step", "ground_state",
+    "gf_hamiltonian",
 ]
 
 
@@ -73,7 +81,8 @@ class Params:
 
     FIELDS = dict(dim=2, n=None, lo=None, hi=None, s=1.0, m=0.0, omega=0.0, beta=0.0,
                   lam=0.0, dt=1e-3, kernel="coulomb", mu=1.0, dip_n=(0.0, 0.0, 1.0),
-                  gamma=(1.0, 1.0, 1.0), gs_delta=1e-3, gs_h=0.125, gs_tmin=None, order=2)
+                  gamma=(1.0, 1.0, 1.0), gs_delta=1e-3, gs_h=0.125, gs_tmin=None, order=2,
+                  lat_amp=0.0, lat_k=(0.0, 0.0, 0.0))
 
     def __init__(self, **kw):
         for k, v in self.FIELDS.items():
@@ -83,6 +92,8 @@ class Params:
         self.hi = tuple(float(v) for v in self.hi)
         g = tuple(float(v) for v in self.gamma)
         self.gamma = g + (1.0,) * (3 - len(g))
+        lk = tuple(float(v) for v in self.lat_k)
+        self.lat_k = lk + (0.0,) * (3 - len(lk))
         if self.kernel == "ddi3d" and self.dim != 3:
             raise ValueError("the 3D dipolar kernel needs dim=3")
         if self.kernel == "ddi3d" and self.mu != 1.0:
@@ -191,7 +202,9 @@ def _gl(a, b, nodes=20):
 
 
 def trap_potential(p, t, gamma=None):
-    """W(x~, t) = V(A(t) x~) (Eq. FSE1_Rot) with V the harmonic trap of Eq. harm_poten."""
+    """W(x~, t) = V(A(t) x~) (Eq. FSE1_Rot) with V the harmonic trap of Eq. harm_poten,
+    plus an optical lattice lat_amp sum_v sin^2(lat_k_v x_v) when lat_amp != 0 (the
+    harmonic-plus-lattice potential of the Section 3.3 example; reading 10)."""
     p = params(p)
     g = p.gamma if gamma is None else tuple(gamma) + p.gamma[len(gamma):]
     X = coords(p)
@@ -200,11 +213,14 @@ def trap_potential(p, t, gamma=None):
     for v in range(p.dim):
         xv = sum(A[v, j] * X[j] for j in range(p.dim))
         V = V + 0.5 * g[v] ** 2 * xv * xv
+        if p.lat_amp != 0.0:
+            V = V + p.lat_amp * np.sin(p.lat_k[v] * xv) ** 2
     return V
 
 
 def trap_integral(p, ta, tb, gamma=None, nodes=16):
-    """P(x~) = int_{ta}^{tb} V(A(tau) x~) dtau (Eq. int_poten) by Gauss-Legendre."""
+    """P(x~) = int_{ta}^{tb} V(A(tau) x~) dtau (Eq. int_poten) by Gauss-Legendre (the
+    numerical quadrature that Section 4.2 names for a general V)."""
     tq, wq = _gl(ta, tb, nodes)
     return sum(w * trap_potential(p, t, gamma) for t, w in zip(tq, wq))
 
@@ -612,3 +628,106 @@ def gradient_adjoint(phi0, target, p, t0, nsteps, gammas=None):
                                    None if gammas is None else gammas[n], Chat)
         dgam[n] = dg
     return g, dgam
+
+
+# ---------------------------------------------------------------------------
+# Ground state by GF-GauSum (Section 3.2, Eqs. gf-eq2, gf-colb2, gffg33): the
+# gradient flow with discrete normalisation, each backward-Euler step solved
+# with BiCGStab on the left-preconditioned system of Eq. precond_type1,
+#   (I + P_Delta A_TF) phi^(1) = P_Delta phi^n / dt,
+#   P_Delta = [1/dt + (-Lap + m^2)^s / 2]^-1,  A_TF = V + beta|phi^n|^2 + lambda Phi^n - Omega L_z,
+# followed by phi^{n+1} = phi^(1) / ||phi^(1)||. The problem is posed in the
+# laboratory frame (no rotating coordinates): V is the trap at t = 0 and the
+# dipole axis is n.
+# ---------------------------------------------------------------------------
+
+def gf_lz(v, p):
+    """L_z v = -i (x d_y v - y d_x v) with spectral derivatives (Eq. AME)."""
+    X = coords(p)
+    return -1j * (X[0] * _spectral_deriv(v, p, 1) - X[1] * _spectral_deriv(v, p, 0))
+
+
+def gf_potential(phi, p, Chat=None):
+    """W = V + beta |phi|^2 + lambda Phi, Phi = U * |phi|^2 (Eq. gf-colb2)."""
+    p = params(p)
+    rho = np.abs(phi) ** 2
+    W = trap_potential(p, 0.0) + p.beta * rho
+    if p.kernel != "none" and p.lam != 0.0:
+        W = W + p.lam * nonlocal_potential(rho, p, kernel_multiplier_instant(p, 0.0, Chat))
+    return W
+
+
+def gf_precond(v, p, dtg):
+    """P_Delta v = F^-1 [F v / (1/dt + (|k|^2 + m^2)^s / 2)]."""
+    return np.fft.ifftn(np.fft.fftn(v) / (1.0 / dtg + 0.5 * kinetic_symbol(p)))
+
+
+def gf_matvec(v, W, p, dtg):
+    """(I + P_Delta A_TF) v (left system of Eq. precond_type1)."""
+    return v + gf_precond(W * v - p.omega * gf_lz(v, p), p, dtg)
+
+
+def bicgstab(apply, b, x0, tol, maxit):
+    """BiCGStab (van der Vorst 1992) for complex systems, inner product sum conj(a) b.
+
+    Stops when ||r|| <= tol ||b||; returns (x, iterations, ||r|| / ||b||)."""
+    dot = lambda a, c: np.vdot(a, c)
+    x = x0.copy()
+    r = b - apply(x)
+    rh = r.copy()
+    bn = math.sqrt(dot(b, b).real)
+    rho_prev = alpha = omega = 1.0
+    v = np.zeros_like(b)
+    pp = np.zeros_like(b)
+    it = 0
+    res = math.sqrt(dot(r, r).real) / bn
+    while it < maxit and res > tol:
+        rho = dot(rh, r)
+        beta = (rho / rho_prev) * (alpha / omega)
+        pp = r + beta * (pp - omega * v)
+        v = apply(pp)
+        alpha = rho / dot(rh, v)
+        s = r - alpha * v
+        t = apply(s)
+        omega = dot(t, s) / dot(t, t)
+        x = x + alpha * pp + omega * s
+        r = s - omega * t
+        rho_prev = rho
+        it += 1
+        res = math.sqrt(dot(r, r).real) / bn
+    return x, it, res
+
+
+def gf_step(phi, p, dtg, Chat=None, inner_tol=1e-13, max_inner=500):
+    """One GFDN step: backward-Euler solve, then normalisation (Eqs. gf-eq2, gffg33)."""
+    p = params(p)
+    W = gf_potential(phi, p, Chat)
+    b = gf_precond(phi / dtg, p, dtg)
+    x, it, _ = bicgstab(lambda v: gf_matvec(v, W, p, dtg), b, phi, inner_tol, max_inner)
+    return x / math.sqrt(mass(x, p)), it
+
+
+def ground_state(phi0, p, dtg, max_outer, tol=0.0, inner_tol=1e-13, max_inner=500):
+    """GF-GauSum iterations from phi0 until max|phi^{n+1} - phi^n| / dt <= tol or max_outer steps.
+
+    Returns (phi, outer steps, total inner iterations, last change)."""
+    p = params(p)
+    Chat = gausum_multiplier(p) if p.kernel != "none" else None
+    phi = phi0 / math.sqrt(mass(phi0, p))
+    inner, change, n = 0, float("inf"), 0
+    while n < max_outer:
+        nxt, it = gf_step(phi, p, dtg, Chat, inner_tol, max_inner)
+        inner += it
+        change = float(np.max(np.abs(nxt - phi))) / dtg
+        phi = nxt
+        n += 1
+        if change <= tol:
+            break
+    return phi, n, inner, change
+
+
+def gf_hamiltonian(phi, p, Chat=None):
+    """H[phi] phi = (-Lap+m^2)^s phi / 2 + W phi - Omega L_z phi (the operator of Eq. gf-eq1)."""
+    p = params(p)
+    kin = 0.5 * np.fft.ifftn(kinetic_symbol(p) * np.fft.fftn(phi))
+    return kin + gf_potential(phi, p, Chat) * phi - p.omega * gf_lz(phi, p)

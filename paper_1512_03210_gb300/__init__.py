@@ -25,6 +25,7 @@ __all__ = [
     "header_functions", "to_params", "fse_plan_profile", "fse_plan_profile_read", "PASS_KINDS",
     "fse_mass_noalloc", "Batch", "fse_batch_create", "fse_batch_set_workspace", "fse_batch_precompute",
     "fse_batch_step", "fse_batch_destroy", "fse_batch_error", "fse_batch_launch_count",
+    "FseGsOpts", "FseGsInfo", "fse_ground_state_workspace", "fse_ground_state",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -44,8 +45,17 @@ class FseParams(ct.Structure):
         ("lambda_", ct.c_double), ("dt", ct.c_double), ("kernel", ct.c_int), ("mu", ct.c_double),
         ("dip_n", ct.c_double * 3), ("gamma", ct.c_double * 3), ("gs_delta", ct.c_double),
         ("gs_h", ct.c_double), ("gs_tmin", ct.c_double), ("prec", ct.c_int), ("renormalize", ct.c_int),
-        ("order", ct.c_int),
+        ("order", ct.c_int), ("lat_amp", ct.c_double), ("lat_k", ct.c_double * 3), ("quad_nodes", ct.c_int),
     ]
+
+
+class FseGsOpts(ct.Structure):
+    _fields_ = [("dt", ct.c_double), ("max_outer", ct.c_int), ("tol", ct.c_double), ("max_inner", ct.c_int),
+                ("inner_tol", ct.c_double)]
+
+
+class FseGsInfo(ct.Structure):
+    _fields_ = [("outer", ct.c_int), ("inner", ct.c_int), ("change", ct.c_double), ("residual", ct.c_double)]
 
 
 class FseObs(ct.Structure):
@@ -117,6 +127,8 @@ def load(build_if_missing: bool = True):
         "fse_batch_destroy": (ct.c_int, [P]),
         "fse_batch_error": (ct.c_char_p, [P]),
         "fse_batch_launch_count": (ct.c_longlong, [P]),
+        "fse_ground_state_workspace": (ct.c_int, [P, ct.POINTER(ct.c_size_t)]),
+        "fse_ground_state": (ct.c_int, [P, P, P, ct.c_size_t, ct.POINTER(FseGsOpts), ct.POINTER(FseGsInfo)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -167,6 +179,11 @@ def to_params(p: dict) -> FseParams:
     fp.prec = PRECS[p.get("prec", "f32")]
     fp.renormalize = int(p.get("renormalize", 0))
     fp.order = int(p.get("order", 2))
+    fp.lat_amp = float(p.get("lat_amp", 0.0))
+    lk = tuple(p.get("lat_k", (0.0, 0.0, 0.0)))
+    for j in range(3):
+        fp.lat_k[j] = float(lk[j]) if j < len(lk) else 0.0
+    fp.quad_nodes = int(p.get("quad_nodes", 0))
     return fp
 
 
@@ -232,6 +249,21 @@ def fse_observables(plan, psi, t: float, gamma=None) -> FseObs:
     _check(load().fse_observables(plan, _ptr(psi), float(t), gp, ct.byref(o)), "fse_observables", plan)
     del keep
     return o
+
+
+def fse_ground_state_workspace(plan) -> int:
+    n = ct.c_size_t(0)
+    _check(load().fse_ground_state_workspace(plan, ct.byref(n)), "fse_ground_state_workspace", plan)
+    return n.value
+
+
+def fse_ground_state(plan, psi, workspace, nbytes: int, dt: float, max_outer: int, tol: float,
+                     max_inner: int, inner_tol: float) -> dict:
+    o = FseGsOpts(float(dt), int(max_outer), float(tol), int(max_inner), float(inner_tol))
+    info = FseGsInfo()
+    _check(load().fse_ground_state(plan, _ptr(psi), _ptr(workspace), int(nbytes), ct.byref(o), ct.byref(info)),
+           "fse_ground_state", plan)
+    return {"outer": info.outer, "inner": info.inner, "change": info.change, "residual": info.residual}
 
 
 def fse_plan_set_stream(plan, stream):
@@ -390,6 +422,15 @@ class Plan:
 
     def observables(self, psi, t: float, gamma=None) -> dict:
         return fse_observables(self.handle, psi, t, gamma).as_dict(self.dim)
+
+    def ground_state(self, psi, dt: float, max_outer: int, tol: float = 0.0, max_inner: int = 500,
+                     inner_tol: float = 1e-12) -> dict:
+        """GF-GauSum ground state (Section 3.2) from the initial guess psi, in place."""
+        import torch
+        assert psi.dtype == self.cdtype and psi.is_contiguous() and tuple(psi.shape) == self.shape
+        nb = fse_ground_state_workspace(self.handle)
+        ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
+        return fse_ground_state(self.handle, psi, ws, nb, dt, max_outer, tol, max_inner, inner_tol)
 
     @property
     def launches(self) -> int:

@@ -89,6 +89,7 @@ extern "C" fse_status fse_step_adjoint(fse_plan_t P, const void* psi_n, void* g,
   x1.pb = pc[1];
   x1.pc = pc[2];
   x1.pe = pc[3];
+  lattice_nodes(P, ta, tb, x1);
   x1.part = dgamma_n ? red + kAdjBase : nullptr;
   x1.part_stride = kAdjStride;
   {

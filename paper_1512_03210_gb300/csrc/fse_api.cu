@@ -223,8 +223,8 @@ fse_status col(fse_plan* P, int kind, int N, int var, const ColArgs& a, const Mu
 
 fse_status xpass(fse_plan* P, int kind, const XArgs& a) {
   if (!twiddle(P, P->nx) || !twiddle(P, 2 * P->nx)) return fail(P, FSE_ERR_INVALID, "no twiddle table for the x pass");
-  static const int kinds[7] = {FSE_PASS_XFWD, FSE_PASS_XINV, FSE_PASS_E, FSE_PASS_A, FSE_PASS_OTHER,
-                               FSE_PASS_OTHER, FSE_PASS_OTHER};
+  static const int kinds[8] = {FSE_PASS_XFWD, FSE_PASS_XINV, FSE_PASS_E, FSE_PASS_A, FSE_PASS_OTHER,
+                               FSE_PASS_OTHER, FSE_PASS_OTHER, FSE_PASS_A};
   cudaEvent_t ev = prof_begin(P);
   cudaError_t e = P->prec == FSE_F32
                       ? launch_xpass<float>(kind, P->nx, a, twiddle(P, P->nx), twiddle(P, 2 * P->nx), P->stream)
@@ -267,7 +267,26 @@ XArgs x_args(fse_plan* P, void* psi, void* spec) {
   a.h0 = P->h[0];
   a.h1 = P->h[1];
   a.h2 = P->dim == 3 ? P->h[2] : 0.0;
+  a.lat_amp = P->p.lat_amp;
+  for (int j = 0; j < 3; ++j) a.lat_k[j] = j < P->dim ? P->p.lat_k[j] : 0.0;
   return a;
+}
+
+// Gauss-Legendre nodes of the window [ta, tb] for the lattice integral (Eq.
+// int_poten by quadrature): weights and (cos, sin)(Omega tau_q). Without
+// rotation the integrand is constant in time and one node is exact.
+void lattice_nodes(fse_plan* P, double ta, double tb, XArgs& a) {
+  if (P->p.lat_amp == 0.0) return;
+  const int n = P->p.omega == 0.0 ? 1 : P->p.quad_nodes;
+  std::vector<double> x, w;
+  gauss_legendre(n, x, w);
+  a.lat_nq = n;
+  for (int q = 0; q < n; ++q) {
+    const double t = 0.5 * (ta + tb) + 0.5 * (tb - ta) * x[q];
+    a.lat_w[q] = 0.5 * (tb - ta) * w[q];
+    a.lat_c[q] = std::cos(P->p.omega * t);
+    a.lat_s[q] = std::sin(P->p.omega * t);
+  }
 }
 
 // Kinetic sub-step of factor f (1: dt/2 as in Eqs. tssp1/tssp3; 2: two merged halves)
@@ -430,8 +449,9 @@ fse_status run_steps(fse_plan* P, void* psi, double t0, int nsteps, const double
     xA.pb = pc[1];
     xA.pc = pc[2];
     xA.pe = pc[3];
+    lattice_nodes(P, ta, tb, xA);
     if (rn) xA.scale = renorm_scale(P);
-    if ((st = xpass(P, XP_A, xA)) != FSE_OK) return st;
+    if ((st = xpass(P, P->p.lat_amp != 0.0 ? XP_AL : XP_A, xA)) != FSE_OK) return st;
   }
   if ((st = kinetic_yz(P, psi, 1.0, dt)) != FSE_OK) return st;
   return xpass(P, XP_INV, xa);
@@ -480,6 +500,9 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
   if (p.kernel == FSE_KERNEL_DDI3D && p.mu != 1.0) return FSE_ERR_INVALID;
   if (p.renormalize != 0 && p.renormalize != 1) return FSE_ERR_INVALID;
   if (p.order != 0 && p.order != 2 && p.order != 4) return FSE_ERR_INVALID;
+  if (!std::isfinite(p.lat_amp) || p.quad_nodes < 0 || p.quad_nodes > 16) return FSE_ERR_INVALID;
+  for (int j = 0; j < 3; ++j)
+    if (!std::isfinite(p.lat_k[j])) return FSE_ERR_INVALID;
   fse_plan* P = new (std::nothrow) fse_plan();
   if (!P) return FSE_ERR_NOMEM;
   P->p = p;
@@ -487,6 +510,7 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
   if (P->p.gs_h <= 0) P->p.gs_h = 0.125;
   if (P->p.kernel == FSE_KERNEL_NONE) P->p.mu = 1.0;
   if (P->p.order == 0) P->p.order = 2;
+  if (P->p.quad_nodes == 0) P->p.quad_nodes = 8;
   // the dropped tail of the sinc quadrature is ~ e^{mu t_min} / mu
   if (P->p.gs_tmin == 0) P->p.gs_tmin = -36.0 / P->p.mu;
   P->stream = reinterpret_cast<cudaStream_t>(stream);

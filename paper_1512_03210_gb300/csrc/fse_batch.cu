@@ -157,6 +157,11 @@ struct fse_batch {
   long long launches = 0;
   std::string err;
   std::vector<BatchRun> desc;  // host staging of the descriptor tables
+  // groups are independent: each runs on its own stream, forked from and
+  // joined back into `stream` with events (created at the first step)
+  std::vector<cudaStream_t> gstream;
+  std::vector<cudaEvent_t> gdone;
+  cudaEvent_t fork = nullptr;
   char* ptr(size_t off) const { return static_cast<char*>(ws) + off; }
 };
 
@@ -177,7 +182,8 @@ fse_status fse_batch_create(const fse_params* runs, int nruns, void* stream, fse
   *workspace_bytes = 0;
   for (int r = 0; r < nruns; ++r) {
     const fse_params& p = runs[r];
-    if (p.dim != 2 || p.prec != FSE_F32 || p.renormalize != 0 || (p.order != 0 && p.order != 2))
+    if (p.dim != 2 || p.prec != FSE_F32 || p.renormalize != 0 || (p.order != 0 && p.order != 2) ||
+        p.lat_amp != 0.0)
       return FSE_ERR_UNSUPPORTED;
     if (p.kernel == FSE_KERNEL_DDI3D || p.kernel == FSE_KERNEL_DDI2D) return FSE_ERR_INVALID;
     if (p.lo[0] != runs[0].lo[0] || p.lo[1] != runs[0].lo[1] || p.hi[0] != runs[0].hi[0] ||
@@ -273,8 +279,27 @@ fse_status fse_batch_step(fse_batch_t B, void* const* psi, double t0, int nsteps
   for (size_t r = 0; r < B->runs.size(); ++r)
     if (!psi[r] || reinterpret_cast<uintptr_t>(psi[r]) % 8 != 0) return bfail(B, FSE_ERR_INVALID, "bad psi pointer");
   if (nsteps == 0) return FSE_OK;
-  cudaStream_t st = B->stream;
-  for (auto& G : B->groups) {
+  const bool multi = B->groups.size() > 1;
+  if (multi && B->gstream.empty()) {
+    cudaError_t e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+    for (size_t g = 0; g < B->groups.size() && e == cudaSuccess; ++g) {
+      cudaStream_t s = nullptr;
+      cudaEvent_t d = nullptr;
+      e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      if (e == cudaSuccess) B->gstream.push_back(s);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
+      if (e == cudaSuccess) B->gdone.push_back(d);
+    }
+    if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("group streams: ") + cudaGetErrorString(e));
+  }
+  if (multi) {
+    cudaError_t e = cudaEventRecord(B->fork, B->stream);
+    for (size_t g = 0; g < B->groups.size() && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(B->gstream[g], B->fork, 0);
+    if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("group fork: ") + cudaGetErrorString(e));
+  }
+  for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+    auto& G = B->groups[gi];
+    const cudaStream_t st = multi ? B->gstream[gi] : B->stream;
     fse_plan* P = G.plan;
     const int nr = (int)G.runs.size();
     // descriptor table of the group
@@ -344,6 +369,11 @@ fse_status fse_batch_step(fse_batch_t B, void* const* psi, double t0, int nsteps
     if ((s = chk(launch_colb(P->ny, 1, ck, mk1, twiddle(P, P->ny), ddesc, nr, 0, 0, 0, st), "batch kinetic")) != FSE_OK)
       return s;
     if ((s = chk(launch_xb(XP_INV, P->nx, xa, twn, tw2n, ddesc, nr, t0, nsteps, st), "batch x")) != FSE_OK) return s;
+    if (multi) {
+      cudaError_t e = cudaEventRecord(B->gdone[gi], st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(B->stream, B->gdone[gi], 0);
+      if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("group join: ") + cudaGetErrorString(e));
+    }
   }
   return FSE_OK;
 }
@@ -351,6 +381,9 @@ fse_status fse_batch_step(fse_batch_t B, void* const* psi, double t0, int nsteps
 fse_status fse_batch_destroy(fse_batch_t B) {
   if (!B) return FSE_OK;
   for (auto& G : B->groups) fse_plan_destroy(G.plan);
+  for (cudaStream_t s : B->gstream) cudaStreamDestroy(s);
+  for (cudaEvent_t e : B->gdone) cudaEventDestroy(e);
+  if (B->fork) cudaEventDestroy(B->fork);
   delete B;
   return FSE_OK;
 }

@@ -61,6 +61,7 @@ fse_status col(fse_plan* P, int kind, int N, int var, const ColArgs& a, const Mu
 fse_status xpass(fse_plan* P, int kind, const XArgs& a);
 int tiles(fse_plan* P, int N, int ncols);
 XArgs x_args(fse_plan* P, void* psi, void* spec);
+void lattice_nodes(fse_plan* P, double ta, double tb, XArgs& a);
 fse_status kinetic_yz(fse_plan* P, void* psi, double f, double dt);
 fse_status nonlocal_yz(fse_plan* P, void* spec, double ta, double tb, bool integrated, const double* mdir,
                        double extra_scale);
@@ -69,6 +70,12 @@ void trap_coefficients(const fse_plan* P, double ta, double tb, const double* ga
 void dipole_matrix(const fse_plan* P, double ta, double tb, double M[6]);
 fse_status run_steps(fse_plan* P, void* psi, double t0, int nsteps, const double* gps);
 double* renorm_part(fse_plan* P);
+// full transform of a field in the plan's layout: forward (dir < 0) or inverse
+// (dir > 0), both unnormalised (fse_observables.cu)
+template <typename Real> fse_status fft_full(fse_plan* P, void* buf, int dir);
+// nonlocal potential Phi = U * |psi|^2 of the un-integrated kernel with dipole
+// axis mdir (null: the plan's axis), written as a real field to phi (fse_observables.cu)
+fse_status nonlocal_field(fse_plan* P, const void* psi, const double* mdir, void* phi);
 const double* renorm_scale(fse_plan* P);
 fse_status renorm_begin(fse_plan* P, const void* psi);
 fse_status renorm_step(fse_plan* P, int count);

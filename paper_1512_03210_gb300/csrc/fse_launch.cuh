@@ -93,6 +93,7 @@ cudaError_t launch_xpass(int kind, int nx, const XArgs& a, const void* twn, cons
       case XP_R: return x_launch<Real, n, XP_R>(a, twn, tw2n, st);     \
       case XP_ADJ1: return x_launch<Real, n, XP_ADJ1>(a, twn, tw2n, st); \
       case XP_ADJ2: return x_launch<Real, n, XP_ADJ2>(a, twn, tw2n, st); \
+      case XP_AL: return x_launch<Real, n, XP_AL>(a, twn, tw2n, st);   \
       default: return x_launch<Real, n, XP_A>(a, twn, tw2n, st);       \
     }
     FSE_X_SIZES(FSE_CASE)

@@ -33,6 +33,7 @@ struct ObsArgs {
   double lo[3], h[3];
   double g2[3];  // gamma_v^2 / 2
   double c, s;   // cos, sin of Omega t
+  double lat_amp, lat_k[3];  // optical lattice lat_amp sum_v sin^2(lat_k[v] x_v)
 };
 
 template <typename Real>
@@ -49,7 +50,11 @@ __global__ void __launch_bounds__(256) k_obs_phys(const typename Cplx<Real>::T* 
     const typename Cplx<Real>::T u = psi[i];
     const double rho = (double)u.x * u.x + (double)u.y * u.y;
     const double X = o.c * x + o.s * y, Y = -o.s * x + o.c * y;
-    const double W = o.g2[0] * X * X + o.g2[1] * Y * Y + o.g2[2] * z * z;
+    double W = o.g2[0] * X * X + o.g2[1] * Y * Y + o.g2[2] * z * z;
+    if (o.lat_amp != 0.0) {
+      const double sx = sin(o.lat_k[0] * X), sy = sin(o.lat_k[1] * Y), sz = sin(o.lat_k[2] * z);
+      W += o.lat_amp * (sx * sx + sy * sy + sz * sz);
+    }
     acc[0] += rho;
     acc[1] += rho * rho;
     acc[2] += W * rho;
@@ -225,6 +230,26 @@ fse_status fft_full(fse_plan* P, void* buf, int dir) {
   return xpass(P, XP_INV, xa);
 }
 
+template fse_status fft_full<float>(fse_plan*, void*, int);
+template fse_status fft_full<double>(fse_plan*, void*, int);
+
+fse_status nonlocal_field(fse_plan* P, const void* psi, const double* mdir, void* phi) {
+  void* tmp = P->ws_ptr(P->off_tmp);
+  void* spec = P->ws_ptr(P->off_spec);
+  cudaError_t e;
+  fse_status st;
+  if ((e = cudaMemcpyAsync(tmp, psi, P->psi_bytes, cudaMemcpyDeviceToDevice, P->stream)) != cudaSuccess)
+    return cuda_fail(P, e, "nonlocal field copy");
+  XArgs xa = x_args(P, tmp, spec);
+  if ((st = xpass(P, XP_FWD, xa)) != FSE_OK) return st;
+  if ((st = xpass(P, XP_E, xa)) != FSE_OK) return st;  // S = R2C of nx^2 rho
+  const double* md = mdir ? mdir : P->p.dip_n;
+  if ((st = nonlocal_yz(P, spec, 0.0, 0.0, false, md, 1.0 / ((double)P->nx * P->nx))) != FSE_OK) return st;
+  XArgs xr = x_args(P, const_cast<void*>(psi), spec);
+  xr.out = phi;
+  return xpass(P, XP_R, xr);
+}
+
 template <typename Real>
 fse_status observables(fse_plan* P, const void* psi_in, double t, const double* gam, fse_obs* out) {
   typedef typename Cplx<Real>::T C;
@@ -247,9 +272,11 @@ fse_status observables(fse_plan* P, const void* psi_in, double t, const double* 
     o.h[j] = P->h[j];
     const double g = j < P->dim ? (gam ? gam[j] : P->p.gamma[j]) : 0.0;
     o.g2[j] = 0.5 * g * g;
+    o.lat_k[j] = j < P->dim ? P->p.lat_k[j] : 0.0;
   }
   o.c = std::cos(P->p.omega * t);
   o.s = std::sin(P->p.omega * t);
+  o.lat_amp = P->p.lat_amp;
   const long long N = (long long)P->nx * P->ny * P->nz;
   const int blocks = (int)std::min<long long>(kRedBlocks, (N + 255) / 256);
 

@@ -24,7 +24,7 @@
 namespace fse {
 
 enum { MUL_NONE = 0, MUL_KIN = 1, MUL_COULOMB = 2, MUL_DDI = 3 };
-enum { XP_FWD = 0, XP_INV = 1, XP_E = 2, XP_A = 3, XP_R = 4, XP_ADJ1 = 5, XP_ADJ2 = 6 };
+enum { XP_FWD = 0, XP_INV = 1, XP_E = 2, XP_A = 3, XP_R = 4, XP_ADJ1 = 5, XP_ADJ2 = 6, XP_AL = 7 };
 
 // Lines per tile: 128-byte rows for the column passes, at most 64 KB of tile.
 __host__ __device__ constexpr int ncol_for(int N, int csize) {
@@ -93,6 +93,14 @@ struct XArgs {
   const void* aux;        // adjoint passes: u1 (output of the first kinetic half step)
   long long part_stride;  // adjoint pass 1: distance between the three gradient slots
   double dp[12];          // adjoint pass 1: dP/dgamma_v = dp[4v] x^2 + dp[4v+1] y^2 + dp[4v+2] x y + dp[4v+3] z^2
+  // optical lattice lat_amp sum_v sin^2(lat_k[v] x_v): its integral over the
+  // window is sum_q lat_w[q] V_lat(x(tau_q)), x = (c x~ + s y~, -s x~ + c y~, z~)
+  // with (c, s) = (lat_c[q], lat_s[q]) = (cos, sin)(Omega tau_q)
+  double lat_amp;
+  double lat_k[3];
+  int lat_nq;
+  double lat_w[16], lat_c[16], lat_s[16];
+  void* out;              // pass R: optional real array receiving varphi (the nonlocal potential)
 };
 
 // Deterministic float64 block sum (blockDim.x a multiple of 32, <= 1024); result in lane 0 of warp 0.
@@ -504,10 +512,41 @@ __device__ __forceinline__ void phase_sincos(float th, float* sn, float* cs) {
 __device__ __forceinline__ void phase_sincos(double th, double* sn, double* cs) { sincos(th, sn, cs); }
 
 template <typename Real>
+__device__ __forceinline__ Real sin_sq(Real v);
+template <> __device__ __forceinline__ float sin_sq(float v) {
+  const float s = sinf(v);
+  return s * s;
+}
+template <> __device__ __forceinline__ double sin_sq(double v) {
+  const double s = sin(v);
+  return s * s;
+}
+
+// Window integral of the optical lattice at the point (X, Y, Z) of the rotating
+// frame (Gauss-Legendre nodes of the window in a.lat_*).
+template <typename Real>
+__device__ __noinline__ Real lattice_integral(const XArgs& a, Real X, Real Y, Real Z) {
+  const Real kx = Real(a.lat_k[0]), ky = Real(a.lat_k[1]);
+  const Real zt = a.lat_k[2] != 0.0 ? sin_sq(Real(a.lat_k[2]) * Z) : Real(0);
+  Real acc = Real(0);
+  for (int q = 0; q < a.lat_nq; ++q) {
+    const Real c = Real(a.lat_c[q]), s = Real(a.lat_s[q]);
+    const Real xr = c * X + s * Y, yr = -s * X + c * Y;
+    acc += Real(a.lat_w[q]) * (sin_sq(kx * xr) + sin_sq(ky * yr) + zt);
+  }
+  return Real(a.lat_amp) * acc;
+}
+
+// P at grid point (x, y, z): the harmonic quadratic form plus, with LAT = 1,
+// the optical lattice (LAT = 2: when lat_amp != 0, decided at run time)
+template <typename Real, int LAT>
 __device__ __forceinline__ Real trap_phase(const XArgs& a, int x, int y, int z) {
   const Real X = Real(a.lo0) + Real(a.h0) * Real(x);
   const Real Y = Real(a.lo1) + Real(a.h1) * Real(y);
   const Real Z = Real(a.lo2) + Real(a.h2) * Real(z);
+  if (LAT == 1 || (LAT == 2 && a.lat_amp != 0.0))
+    return Real(a.pa) * X * X + Real(a.pb) * Y * Y + Real(a.pc) * X * Y + Real(a.pe) * Z * Z +
+           lattice_integral<Real>(a, X, Y, Z);
   return Real(a.pa) * X * X + Real(a.pb) * Y * Y + Real(a.pc) * X * Y + Real(a.pe) * Z * Z;
 }
 
@@ -589,7 +628,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
           const long long o = (long long)lg * NX + x;
           const C u = u1p[o];
           const C g = psi[o];
-          const Real th = Real(a.beta_dt) * (u.x * u.x + u.y * u.y) + Real(a.lam) * vphi[it] + trap_phase<Real>(a, x, yl, zl);
+          const Real th = Real(a.beta_dt) * (u.x * u.x + u.y * u.y) + Real(a.lam) * vphi[it] + trap_phase<Real, 2>(a, x, yl, zl);
           Real sn, cs;
           sincos(th, &sn, &cs);
           const C u2 = mk(u.x * cs + u.y * sn, u.y * cs - u.x * sn);
@@ -640,7 +679,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
     }
   } else {
     // XP_A / XP_R: varphi from the cropped C2R of S
-    if (KIND == XP_A && tid == 0 && l0 < a.nlines) {
+    if ((KIND == XP_A || KIND == XP_AL) && tid == 0 && l0 < a.nlines) {
       // the tile's rows of psi (contiguous) move to L2 while the C2R runs
       const int nl = min(NCOL, a.nlines - l0);
       prefetch_l2_bulk(psi + (long long)l0 * NX, (unsigned)(nl * NX * sizeof(C)));
@@ -650,6 +689,19 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
     for (int it = 0; it < PER; ++it) vphi[it] = Real(0);
     if (a.use_spec) c2r_rows<Real, NX>(a, buf, l0, tw2n, vphi);
     if constexpr (KIND == XP_R) {
+      if (a.out) {
+        // varphi itself, as a real field in the layout of psi
+        Real* phi = reinterpret_cast<Real*>(a.out);
+#pragma unroll
+        for (int it = 0; it < PER; ++it) {
+          const int idx = tid + it * NT;
+          if ((TOT % NT) == 0 || idx < TOT) {
+            const int l = idx / NX, x = idx % NX;
+            if (l0 + l < a.nlines) phi[(long long)(l0 + l) * NX + x] = vphi[it];
+          }
+        }
+      }
+      if (!a.part) return;
       // sum over the tile of varphi * |psi|^2 (nonlocal interaction energy density)
       double acc = 0.0;
 #pragma unroll
@@ -680,7 +732,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
             line_yz(y0, z0, l, a.ny, yl, zl);
             const C u = psi[(long long)lg * NX + x];
             const Real rho = u.x * u.x + u.y * u.y;
-            const Real th = Real(a.beta_dt) * rho + Real(a.lam) * vphi[it] + trap_phase<Real>(a, x, yl, zl);
+            const Real th = Real(a.beta_dt) * rho + Real(a.lam) * vphi[it] + trap_phase<Real, KIND == XP_AL ? 1 : 0>(a, x, yl, zl);
             Real sn, cs;
             phase_sincos(th, &sn, &cs);
             u2 = unit_mul(u, cs, -sn, false);

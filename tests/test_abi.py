@@ -64,6 +64,10 @@ def test_plan_validation_on_host():
     assert _create(dict(good, kernel="ddi2d"))[0] == 0
     assert _create(dict(good, kernel="ddi2d", mu=0.5))[0] == 1
     assert _create(dict(d3, kernel="ddi2d"))[0] == 1
+    # optical lattice: finite parameters, 0..16 quadrature nodes
+    assert _create(dict(good, lat_amp=10.0, lat_k=(3.14, 3.14), quad_nodes=12))[0] == 0
+    assert _create(dict(good, lat_amp=10.0, quad_nodes=17))[0] == 1
+    assert _create(dict(good, lat_amp=float("nan")))[0] == 1
     # splitting order: 2 (TS2-GauSum) or 4 (triple jump)
     assert _create(dict(good, order=4))[0] == 0
     assert _create(dict(good, order=3))[0] == 1

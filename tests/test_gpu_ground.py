@@ -1,0 +1,78 @@
+"""GPU GF-GauSum ground states (fse_ground_state, Section 3.2) against the FP64 oracle, through the C ABI.
+
+A fixed number of normalised gradient-flow steps, each inner BiCGStab solve
+converged to 1e-13, gives iterates that agree with the oracle's to rounding
+(the inner Krylov paths may differ; the solutions do not). Converged runs are
+compared through the ground state's density and energy, which are unique.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _guess(p):
+    X = O.coords(p)
+    e = sum(-0.5 * (1.0 + 0.15 * j) * (X[j] - 0.2 * (j + 1)) ** 2 for j in range(p.dim))
+    return np.exp(e).astype(complex)
+
+
+def _run(lib, d, guess, **kw):
+    plan = lib.Plan(d)
+    x = plan.to_device(guess)
+    info = plan.ground_state(x, **kw)
+    torch.cuda.synchronize()
+    return x.cpu().numpy().astype(np.complex128), info, plan, x
+
+
+CASES = {
+    "2d_coulomb_rot": dict(dim=2, n=(48, 48), lo=(-6.0, -6.0), hi=(6.0, 6.0), s=1.0, omega=0.4, beta=40.0,
+                           lam=8.0, kernel="coulomb", gamma=(1.0, 1.1), prec="f64"),
+    "2d_lattice": dict(dim=2, n=(64, 64), lo=(-4.0, -4.0), hi=(4.0, 4.0), s=0.8, omega=0.0, beta=0.0,
+                       lam=16.0, kernel="coulomb", gamma=(1.0, 1.0), lat_amp=10.0,
+                       lat_k=(math.pi, math.pi), prec="f64"),
+    "3d_ddi_rot": dict(dim=3, n=(16, 16, 16), lo=(-4.0,) * 3, hi=(4.0,) * 3, s=0.9, omega=0.3, beta=20.0,
+                       lam=10.0, kernel="ddi3d", dip_n=(0.6, 0.0, 0.8), gamma=(1.0, 1.0, 1.5), prec="f64"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fixed_steps_match_oracle(lib, name):
+    d = CASES[name]
+    p = O.params(d)
+    dtg, K = 0.1, 4
+    ref, n, inner, change = O.ground_state(_guess(p), p, dtg, K, tol=0.0, inner_tol=1e-13)
+    got, info, _, _ = _run(lib, d, _guess(p), dt=dtg, max_outer=K, tol=0.0, max_inner=500, inner_tol=1e-13)
+    assert info["outer"] == K and info["residual"] <= 1e-13
+    rel = np.linalg.norm((got - ref).ravel()) / np.linalg.norm(ref.ravel())
+    assert rel < 1e-10, rel
+    assert abs(info["change"] - change) < 1e-8 * max(1.0, change)
+
+
+def test_converged_ground_state_matches_oracle(lib):
+    """Run both to max|phi^{n+1} - phi^n|/dt <= 1e-9: equal densities and energies."""
+    d = CASES["2d_lattice"]
+    p = O.params(d)
+    ref, n, inner, change = O.ground_state(_guess(p), p, 0.25, 3000, tol=1e-9, inner_tol=1e-12)
+    got, info, plan, x = _run(lib, d, _guess(p), dt=0.25, max_outer=3000, tol=1e-9, max_inner=500, inner_tol=1e-12)
+    assert info["change"] <= 1e-9
+    assert np.max(np.abs(np.abs(got) ** 2 - np.abs(ref) ** 2)) < 1e-7 * np.max(np.abs(ref) ** 2)
+    e_ref = O.observables(ref, p, 0.0)["energy"]
+    e_gpu = plan.observables(x, 0.0)["energy"]
+    assert abs(e_gpu - e_ref) < 1e-9 * abs(e_ref)
+
+
+def test_float32_ground_state_energy(lib):
+    """float32 path: the converged energy agrees with the float64 oracle's to 1e-5."""
+    d = dict(CASES["2d_coulomb_rot"], prec="f32")
+    p = O.params(d)
+    ref, *_ = O.ground_state(_guess(p), p, 0.2, 3000, tol=1e-9, inner_tol=1e-12)
+    got, info, plan, x = _run(lib, d, _guess(p), dt=0.2, max_outer=400, tol=2e-4, max_inner=200, inner_tol=1e-6)
+    e_ref = O.observables(ref, p, 0.0)["energy"]
+    e_gpu = plan.observables(x, 0.0)["energy"]
+    assert abs(e_gpu - e_ref) < 1e-5 * abs(e_ref), (e_gpu, e_ref, info)

@@ -30,6 +30,9 @@ CASES = {
                            beta=30.0, lam=10.0, dt=1e-3, kernel="coulomb", gamma=(1.0, 1.1, 1.3), prec="f32"),
     "2d_ddi_f64": dict(dim=2, n=(48, 48), lo=(-6.0, -6.0), hi=(6.0, 6.0), s=0.8, omega=0.7, beta=20.0,
                        lam=15.0, dt=1e-3, kernel="ddi2d", dip_n=(0.48, -0.36, 0.8), gamma=(1.0, 1.3), prec="f64"),
+    "2d_lattice_f64": dict(dim=2, n=(64, 64), lo=(-6.0, -6.0), hi=(6.0, 6.0), s=0.9, omega=0.5, beta=20.0,
+                           lam=5.0, dt=1e-3, kernel="coulomb", gamma=(1.0, 1.0), lat_amp=10.0,
+                           lat_k=(math.pi, math.pi), prec="f64"),
     "2d_none_f64": dict(dim=2, n=(32, 32), lo=(-6.0, -6.0), hi=(6.0, 6.0), s=1.0, omega=0.3, beta=10.0,
                         lam=0.0, dt=1e-3, kernel="none", gamma=(1.0, 1.0), prec="f64"),
 }

@@ -121,6 +121,19 @@ def test_ddi_2d_matches_oracle(lib, prec, tol):
     assert _rel(got, ref) < tol * 3
 
 
+@pytest.mark.parametrize("dim,prec,tol", [(2, "f64", 2e-12), (3, "f64", 2e-12), (3, "f32", 5e-6)])
+def test_optical_lattice_matches_oracle(lib, dim, prec, tol):
+    """Harmonic plus optical lattice V (Section 3.3 example's form) in the rotating frame:
+    P = int V(A(tau) x~) dtau by Gauss-Legendre quadrature (Section 4.2, general V)."""
+    lat = dict(lat_amp=10.0, lat_k=(math.pi, 0.8 * math.pi, 0.5 * math.pi)[:dim], prec=prec)
+    d = _case2d(**lat) if dim == 2 else _case3d(**lat)
+    p = O.params(d)
+    psi0 = _gauss(p)
+    ref = O.evolve(psi0, p, 0.05, 3)
+    got, _ = _run_gpu(lib, d, psi0, 0.05, 3)
+    assert _rel(got, ref) < tol * 3
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_kinetic_mass_term_f64_matches_oracle(lib, dim):
     """(-Lap + m^2)^s with m > 0 (Eq. SFSE)."""

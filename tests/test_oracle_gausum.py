@@ -354,3 +354,29 @@ def test_ddi_2d_integrated_kernel_matches_instant_quadrature():
     t = 0.5 * (tb - ta) * tq + 0.5 * (ta + tb)
     ref = sum(0.5 * (tb - ta) * w * O.kernel_multiplier_instant(p, tt, C) for tt, w in zip(t, wq))
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_lattice_trap_integral_quadrature():
+    """Harmonic plus optical lattice V = sum_v (gamma_v^2 x_v^2/2 + A sin^2(k_v x_v)) in the
+    rotating frame: P = int V(A(tau) x~) dtau against adaptive quadrature (Section 4.2,
+    quadrature for a general V); Omega = 0 gives dt V; the Section 3.3 example's V."""
+    p = O.Params(dim=3, n=(6, 6, 4), lo=(-3.0,) * 3, hi=(3.0,) * 3, omega=1.1, gamma=(1.0, 1.2, 2.0),
+                 lat_amp=10.0, lat_k=(math.pi, 0.8 * math.pi, 0.5 * math.pi))
+    ta, tb = 0.21, 0.21 + 0.07
+    P = O.trap_integral(p, ta, tb)
+    X = O.coords(p)
+    for idx in [(0, 0, 0), (1, 2, 3), (3, 5, 1), (2, 4, 5)]:
+        x = np.array([X[j][idx] for j in range(3)])
+
+        def f(t):
+            y = O.rotation(p.omega, t, 3) @ x
+            return sum(0.5 * p.gamma[v] ** 2 * y[v] ** 2 + p.lat_amp * math.sin(p.lat_k[v] * y[v]) ** 2
+                       for v in range(3))
+        ref = integrate.quad(f, ta, tb, epsabs=1e-17, epsrel=1e-14)[0]
+        assert abs(P[idx] - ref) < 1e-14 * max(1, abs(ref))
+    still = O.Params(dim=2, n=(8, 8), lo=(-2.0, -2.0), hi=(2.0, 2.0), omega=0.0, gamma=(1.0, 1.0),
+                     lat_amp=10.0, lat_k=(math.pi, math.pi))
+    X = O.coords(still)
+    V = (X[0] ** 2 + X[1] ** 2) / 2 + 10 * (np.sin(math.pi * X[0]) ** 2 + np.sin(math.pi * X[1]) ** 2)
+    assert np.max(np.abs(O.trap_potential(still, 0.0) - V)) < 1e-13
+    assert np.max(np.abs(O.trap_integral(still, 0.3, 0.35) - 0.05 * V)) < 1e-13
