@@ -35,6 +35,8 @@ if ROOT not in sys.path:
 METRIC = "split steps/s, 256³ dipolar FSE: FP32 vs FP64 path, same accuracy; % HBM roofline"
 UNIT = "split steps/s"
 WORKLOAD = "3d_dipolar_256"
+GS_WORKLOAD = "gs_2d_512"   # GF-GauSum ground state, 512^2 on [-32,32]^2, dt = 1e-3
+GS_INNER_TOL = 1e-12
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
@@ -42,7 +44,7 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 # CPU side: the FP64 oracle on a bounded sample (spawned before any GPU call)
 # ---------------------------------------------------------------------------
 
-def _oracle_sample(nsteps: int, q) -> None:
+def _oracle_sample(nsteps: int, gs_steps: int, q) -> None:
     try:
         import numpy as np  # noqa: F401
         import fse_inputs as I
@@ -57,15 +59,27 @@ def _oracle_sample(nsteps: int, q) -> None:
         for n in range(nsteps):
             psi = O.split_step(psi, p, n * p.dt, None, C)
         dt = time.perf_counter() - t0
-        q.put({"ok": True, "seconds": dt, "steps": nsteps, "precompute_s": t_pre})
+        r = {"ok": True, "seconds": dt, "steps": nsteps, "precompute_s": t_pre}
+        if gs_steps > 0:
+            # the ground-state workload: GF-GauSum steps of the oracle
+            pg = O.params(I.workload(GS_WORKLOAD))
+            phi = I.psi0(GS_WORKLOAD)
+            Cg = O.gausum_multiplier(pg)
+            t0 = time.perf_counter()
+            inner = 0
+            for _ in range(gs_steps):
+                phi, it = O.gf_step(phi, pg, pg.dt, Cg, GS_INNER_TOL, 500)
+                inner += it
+            r["gs"] = {"seconds": time.perf_counter() - t0, "steps": gs_steps, "inner": inner}
+        q.put(r)
     except Exception as e:  # noqa: BLE001 - reported in the JSON line
         q.put({"ok": False, "error": repr(e)})
 
 
-def start_oracle(nsteps: int):
+def start_oracle(nsteps: int, gs_steps: int = 0):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    proc = ctx.Process(target=_oracle_sample, args=(nsteps, q), daemon=True)
+    proc = ctx.Process(target=_oracle_sample, args=(nsteps, gs_steps, q), daemon=True)
     proc.start()
     return proc, q
 
@@ -181,13 +195,18 @@ def step_model_bytes(d: dict) -> int:
     return b["A"] + b["kin"] + b["E"] + b["khat"]
 
 
+# sources that define the split step's kernels and their launch arguments; the
+# DRAM counters in profiles/traffic.json stand only while these are unchanged
+STEP_SOURCES = ("fse_api.cu", "fse_col_f32.cu", "fse_col_f64.cu", "fse_fft.cuh", "fse_internal.h",
+                "fse_launch.cuh", "fse_passes.cuh", "fse_precompute.cu", "fse_x_f32.cu", "fse_x_f64.cu")
+
+
 def source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1512_03210_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in STEP_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -257,6 +276,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--oracle-steps", type=int, default=1)
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--gs-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -270,7 +290,7 @@ def main():
     # the oracle process is spawned before the first GPU call
     oracle = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        oracle = start_oracle(args.oracle_steps)
+        oracle = start_oracle(args.oracle_steps, 2 if args.gs_steps > 0 else 0)
 
     import numpy as np
     import torch
@@ -398,11 +418,37 @@ def main():
                    "sizes": sorted({r["n"][0] for r in runs})}
         del bt, xs
 
+    # GF-GauSum ground state (Section 3.2): normalised gradient-flow steps, each a
+    # BiCGStab solve through the library's FFT passes (the call synchronises)
+    gs = None
+    if args.gs_steps > 0:
+        dg = I.workload(GS_WORKLOAD)
+        pg = fse.Plan(dg, stream=stream, device=dev)
+        xg = pg.to_device(I.psi0(GS_WORKLOAD))
+        nbg = fse.fse_ground_state_workspace(pg.handle)
+        wsg = torch.empty(nbg, dtype=torch.uint8, device=dev)
+        fse.fse_ground_state(pg.handle, xg, wsg, nbg, dg["dt"], 2, 0.0, 500, GS_INNER_TOL)
+        lg = pg.launches
+        t0g = time.perf_counter()
+        info = fse.fse_ground_state(pg.handle, xg, wsg, nbg, dg["dt"], args.gs_steps, 0.0, 500, GS_INNER_TOL)
+        sec = time.perf_counter() - t0g
+        gs = {"workload": GS_WORKLOAD, "grid": list(dg["n"]), "dtype": "f64", "gf_steps": info["outer"],
+              "gf_steps_per_s": info["outer"] / sec, "ms_per_gf_step": 1000 * sec / max(1, info["outer"]),
+              "inner_iterations": info["inner"], "ms_per_inner_iteration": 1000 * sec / max(1, info["inner"]),
+              "last_change": info["change"], "launches": pg.launches - lg,
+              "note": "host-timed: every BiCGStab iteration reads its inner products back"}
+        del pg, xg, wsg
+
     if rank != 0:
         return 0
     cb = None
     if oracle is not None:
-        cb = oracle_baseline_dict(finish_oracle(*oracle))
+        ro = finish_oracle(*oracle)
+        cb = oracle_baseline_dict(ro)
+        if gs is not None and ro.get("gs"):
+            g0 = ro["gs"]
+            gs["oracle"] = {"gf_steps_per_s": g0["steps"] / g0["seconds"], "steps": g0["steps"],
+                            "inner_iterations": g0["inner"], "cores": 1, "kind": "oracle"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -414,7 +460,7 @@ def main():
         "grid_point_steps_per_s": value * 256 ** 3,
         "model_bytes_per_step": step_bytes,
         "step_roofline_frac": step_bytes * value / world / 1e9 / peak,
-        "roofline": roofline, "kernels": kernels, "f64": f64, "e2e": e2e, "batched_2d": batched,
+        "roofline": roofline, "kernels": kernels, "f64": f64, "e2e": e2e, "batched_2d": batched, "ground_state": gs,
         "cpu_baseline": cb, "gpu_launches": launches, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)

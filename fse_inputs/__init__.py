@@ -96,6 +96,10 @@ WORKLOADS = {
         dim=2, n=(256, 256), lo=(-8.0, -8.0), hi=(8.0, 8.0), s=0.6, m=0.0, omega=0.7,
         beta=100.0, lam=10.0, dt=1e-3, kernel="coulomb", mu=1.0, dip_n=(0.0, 0.0, 1.0),
         gamma=(1.0, 1.0), steps=200, seed=3, prec="f32"),
+    "gs_2d_512": dict(
+        dim=2, n=(512, 512), lo=(-32.0, -32.0), hi=(32.0, 32.0), s=0.8, m=0.0, omega=0.0,
+        beta=10.0, lam=10.0, dt=1e-3, kernel="coulomb", mu=1.0, dip_n=(0.0, 0.0, 1.0),
+        gamma=(1.0, 1.0), steps=20, seed=5, prec="f64", init="gs_guess"),
     "3d_dipolar_256": dict(
         dim=3, n=(256, 256, 256), lo=(-12.0,) * 3, hi=(12.0,) * 3, s=0.6, m=0.0, omega=0.9,
         beta=500.0, lam=100.0, dt=2.5e-4, kernel="ddi3d", mu=1.0, dip_n=(_SQ, 0.0, _SQ),
@@ -134,6 +138,9 @@ def psi0(name_or_params, **override) -> np.ndarray:
     """Initial wave function (complex128, shape [nz][ny][nx] or [ny][nx], x fastest).
 
     * 2D workloads: pi^{-1/2} exp(-((x-1)^2+y^2)/2) (unit mass).
+    * ``gs_2d_512`` (ground state): ((1-Omega) phi_ho + Omega phi^v_ho) / norm with
+      phi_ho = pi^{-1/2} e^{-|x|^2/2}, phi^v_ho = (x+iy) phi_ho (the shape of the
+      paper's initial guess for its ground-state runs).
     * ``3d_dipolar_128``: anisotropic Gaussian (gx gy gz)^{1/4} pi^{-3/4}
       exp(-sum g_v v^2/2) times exp(i 1e-3 xi), xi i.i.d. N(0,1) per point.
     * ``3d_dipolar_256``: Thomas-Fermi-like envelope sqrt(max(0,1-sum (v/R_v)^2)),
@@ -150,6 +157,12 @@ def psi0(name_or_params, **override) -> np.ndarray:
         kind = p.get("init", "gauss2d" if p["dim"] == 2 else "gauss3d")
     X, Y, Z = _mesh(p)
     rng = SplitMix64(p.get("seed", 0))
+    if p["dim"] == 2 and (kind == "gs_2d_512" or p.get("init") == "gs_guess"):
+        # ground-state initial guess ((1-Omega) phi_ho + Omega phi^v_ho), normalised
+        om = p.get("omega", 0.0)
+        ho = np.pi ** -0.5 * np.exp(-(X ** 2 + Y ** 2) / 2)
+        psi = ((1 - om) * ho + om * (X + 1j * Y) * ho).astype(np.complex128)
+        return psi / math.sqrt(_mass(p, psi))
     if p["dim"] == 2 and kind != "vortex3d":
         x0 = p.get("x0", (1.0, 0.0))
         return (np.pi ** -0.5 * np.exp(-((X - x0[0]) ** 2 + (Y - x0[1]) ** 2) / 2)).astype(np.complex128)

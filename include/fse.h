@@ -278,6 +278,16 @@ fse_status fse_ground_state_workspace(fse_plan_t plan, size_t* bytes);
 fse_status fse_ground_state(fse_plan_t plan, void* psi, void* workspace, size_t workspace_bytes,
                             const fse_gs_opts* opts, fse_gs_info* info);
 
+/* Initial data of the dynamics runs (Section 4.3, Eq. ini_dyn): psi <-
+ * psi(x - x0) exp(i k . x), the translation taken spectrally (the Nyquist mode
+ * of each axis takes cos(k_N x0_j), the mean of its two aliases) and the kick
+ * exactly; e.g. x0 = (3, 3), k = v0 (0.8, 0.5) turns a ground state into the
+ * paper's shifted and moving state. x0 and k are host arrays [dim] (nullable:
+ * no shift / no kick); psi is device, plan layout. Asynchronous. Errors:
+ * FSE_ERR_INVALID (null or misaligned psi, precompute not run, non-finite x0
+ * or k). */
+fse_status fse_shift_kick(fse_plan_t plan, void* psi, const double* x0, const double* k);
+
 /* Largest npoints accepted by fse_mass_noalloc (4096 partials of 65536 points). */
 #define FSE_NOALLOC_MAX_POINTS (4096LL * 65536LL)
 

@@ -51,6 +51,8 @@ Readings where the paper is silent or ambiguous (each pinned by a test):
 10. A general V (Section 4.2: P by numerical quadrature): the harmonic trap
    plus an optical lattice lat_amp sum_v sin^2(lat_k_v x_v) in the lab frame,
    the potential of the harmonic-plus-lattice example of Section 3.3.
+11. Eq. ini_dyn shifts a ground state by x0 off the grid: the translation is
+   spectral, and the Nyquist mode of each axis takes cos(k_N x0_j).
 
 The time-integrated trap P (Eq. int_poten) and dipole matrix
 M = int m m^T dtau (Eq. Kernel_Rot / solu_step2_conv) are computed here by
@@ -72,7 +74,7 @@ __all__ = [
     "observables", "com_velocity_spectral", "mass",
     "adjoint_split_step", "evolve_with_states", "objective_overlap", "gradient_adjoint",
     "gf_lz", "gf_potential", "gf_precond", "gf_matvec", "bicgstab", "gf_step", "ground_state",
-    "gf_hamiltonian",
+    "gf_hamiltonian", "shift_kick",
 ]
 
 
@@ -731,3 +733,28 @@ def gf_hamiltonian(phi, p, Chat=None):
     p = params(p)
     kin = 0.5 * np.fft.ifftn(kinetic_symbol(p) * np.fft.fftn(phi))
     return kin + gf_potential(phi, p, Chat) * phi - p.omega * gf_lz(phi, p)
+
+
+def shift_kick(phi, p, x0=None, k=None):
+    """phi(x - x0) exp(i k.x): the shifted and kicked initial data of Eq. ini_dyn.
+
+    The translation uses the shift theorem on the periodic grid (reading 11);
+    at the Nyquist index of each axis the factor is cos(k_N x0_j), the mean of
+    the two aliases +-k_N. The kick multiplies pointwise."""
+    p = params(p)
+    out = np.asarray(phi, dtype=complex)
+    if x0 is not None and any(x0[j] != 0.0 for j in range(p.dim)):
+        fac = 1.0
+        for j in range(p.dim):
+            n = p.n[j]
+            kj = _freq(n, p.hi[j] - p.lo[j])
+            f = np.exp(-1j * kj * x0[j])
+            f[n // 2] = math.cos(kj[n // 2] * x0[j])
+            shape = [1] * p.dim
+            shape[p.dim - 1 - j] = n
+            fac = fac * f.reshape(shape)
+        out = np.fft.ifftn(fac * np.fft.fftn(out))
+    if k is not None and any(k[j] != 0.0 for j in range(p.dim)):
+        X = coords(p)
+        out = out * np.exp(1j * sum(k[j] * X[j] for j in range(p.dim)))
+    return out

@@ -25,7 +25,7 @@ __all__ = [
     "header_functions", "to_params", "fse_plan_profile", "fse_plan_profile_read", "PASS_KINDS",
     "fse_mass_noalloc", "Batch", "fse_batch_create", "fse_batch_set_workspace", "fse_batch_precompute",
     "fse_batch_step", "fse_batch_destroy", "fse_batch_error", "fse_batch_launch_count",
-    "FseGsOpts", "FseGsInfo", "fse_ground_state_workspace", "fse_ground_state",
+    "FseGsOpts", "FseGsInfo", "fse_ground_state_workspace", "fse_ground_state", "fse_shift_kick",
 ]
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -129,6 +129,7 @@ def load(build_if_missing: bool = True):
         "fse_batch_launch_count": (ct.c_longlong, [P]),
         "fse_ground_state_workspace": (ct.c_int, [P, ct.POINTER(ct.c_size_t)]),
         "fse_ground_state": (ct.c_int, [P, P, P, ct.c_size_t, ct.POINTER(FseGsOpts), ct.POINTER(FseGsInfo)]),
+        "fse_shift_kick": (ct.c_int, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -264,6 +265,12 @@ def fse_ground_state(plan, psi, workspace, nbytes: int, dt: float, max_outer: in
     _check(load().fse_ground_state(plan, _ptr(psi), _ptr(workspace), int(nbytes), ct.byref(o), ct.byref(info)),
            "fse_ground_state", plan)
     return {"outer": info.outer, "inner": info.inner, "change": info.change, "residual": info.residual}
+
+
+def fse_shift_kick(plan, psi, x0=None, k=None):
+    a = (ct.c_double * 3)(*((tuple(x0) + (0.0,) * 3)[:3])) if x0 is not None else None
+    b = (ct.c_double * 3)(*((tuple(k) + (0.0,) * 3)[:3])) if k is not None else None
+    _check(load().fse_shift_kick(plan, _ptr(psi), a, b), "fse_shift_kick", plan)
 
 
 def fse_plan_set_stream(plan, stream):
@@ -431,6 +438,11 @@ class Plan:
         nb = fse_ground_state_workspace(self.handle)
         ws = torch.empty(nb, dtype=torch.uint8, device=self.device)
         return fse_ground_state(self.handle, psi, ws, nb, dt, max_outer, tol, max_inner, inner_tol)
+
+    def shift_kick(self, psi, x0=None, k=None):
+        """psi <- psi(x - x0) exp(i k.x) in place (Eq. ini_dyn)."""
+        fse_shift_kick(self.handle, psi, x0, k)
+        return psi
 
     @property
     def launches(self) -> int:

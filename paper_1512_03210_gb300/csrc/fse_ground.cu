@@ -1,4 +1,5 @@
-// fse_ground.cu -- ground state by GF-GauSum (Section 3.2, Eqs. gf-eq2, gf-colb2, gffg33).
+// fse_ground.cu -- ground state by GF-GauSum (Section 3.2, Eqs. gf-eq2, gf-colb2, gffg33),
+// and the shifted and kicked initial data of the dynamics runs (Section 4.3, Eq. ini_dyn).
 //
 // Gradient flow with discrete normalisation, discretised by backward Euler:
 //   (1/dt + (-Lap + m^2)^s / 2 + W_n - Omega L_z) phi^(1) = phi^n / dt,
@@ -196,6 +197,87 @@ __global__ void __launch_bounds__(256) k_gs_final(const double* part, int count,
   if (threadIdx.x == 0) out[blockIdx.x] = red[0];
 }
 
+// Spectral translation by x0 (the Nyquist mode takes cos(k_N x0), the mean of
+// its two aliases) and 1/N for the unnormalised inverse.
+template <typename Real>
+__global__ void k_gs_shift(typename Cplx<Real>::T* __restrict__ sp, GsGrid g, double3 x0, double inv_n) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    gs_index(i, g, ix, iy, iz);
+    const int nn[3] = {g.nx, g.ny, g.nz};
+    const int id[3] = {ix, iy, iz};
+    const double xs[3] = {x0.x, x0.y, x0.z};
+    double re = inv_n, im = 0.0;
+    for (int j = 0; j < 3; ++j) {
+      if (nn[j] == 1 || xs[j] == 0.0) continue;
+      const double k = g.dk[j] * wrap_index(id[j], nn[j]);
+      double c, s;
+      if (2 * id[j] == nn[j]) {
+        c = cos(k * xs[j]);
+        s = 0.0;
+      } else {
+        sincos(-k * xs[j], &s, &c);
+      }
+      const double r2 = re * c - im * s, i2 = re * s + im * c;
+      re = r2;
+      im = i2;
+    }
+    const typename Cplx<Real>::T u = sp[i];
+    sp[i] = mk(Real(re * u.x - im * u.y), Real(re * u.y + im * u.x));
+  }
+}
+
+// psi *= exp(i k . x)
+template <typename Real>
+__global__ void k_gs_kick(typename Cplx<Real>::T* __restrict__ psi, GsGrid g, double3 kv) {
+  const long long N = (long long)g.nx * g.ny * g.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    gs_index(i, g, ix, iy, iz);
+    const double ph = kv.x * (g.lo[0] + g.h[0] * ix) + kv.y * (g.lo[1] + g.h[1] * iy) + kv.z * (g.lo[2] + g.h[2] * iz);
+    double s, c;
+    sincos(ph, &s, &c);
+    const typename Cplx<Real>::T u = psi[i];
+    psi[i] = mk(Real(c * u.x - s * u.y), Real(c * u.y + s * u.x));
+  }
+}
+
+GsGrid gs_grid(const fse_plan* P) {
+  GsGrid g;
+  g.nx = P->nx;
+  g.ny = P->ny;
+  g.nz = P->nz;
+  for (int j = 0; j < 3; ++j) {
+    g.lo[j] = j < P->dim ? P->p.lo[j] : 0.0;
+    g.h[j] = j < P->dim ? P->h[j] : 0.0;
+    g.dk[j] = j < P->dim ? 2 * kPi / (P->p.hi[j] - P->p.lo[j]) : 0.0;
+  }
+  return g;
+}
+
+template <typename Real>
+fse_status shift_kick(fse_plan* P, void* psi, const double* x0, const double* kv) {
+  const GsGrid g = gs_grid(P);
+  const long long N = (long long)P->nx * P->ny * P->nz;
+  const int blocks = (int)std::min<long long>(kGsBlocks, (N + 255) / 256);
+  fse_status st;
+  if (x0 && (x0[0] != 0.0 || x0[1] != 0.0 || (P->dim == 3 && x0[2] != 0.0))) {
+    if ((st = fft_full<Real>(P, psi, -1)) != FSE_OK) return st;
+    k_gs_shift<Real><<<blocks, 256, 0, P->stream>>>(static_cast<typename Cplx<Real>::T*>(psi), g,
+                                                    make_double3(x0[0], x0[1], P->dim == 3 ? x0[2] : 0.0),
+                                                    1.0 / (double)N);
+    if ((st = launched(P, cudaGetLastError(), "shift")) != FSE_OK) return st;
+    if ((st = fft_full<Real>(P, psi, +1)) != FSE_OK) return st;
+  }
+  if (kv && (kv[0] != 0.0 || kv[1] != 0.0 || (P->dim == 3 && kv[2] != 0.0))) {
+    k_gs_kick<Real><<<blocks, 256, 0, P->stream>>>(static_cast<typename Cplx<Real>::T*>(psi), g,
+                                                   make_double3(kv[0], kv[1], P->dim == 3 ? kv[2] : 0.0));
+    if ((st = launched(P, cudaGetLastError(), "kick")) != FSE_OK) return st;
+  }
+  return FSE_OK;
+}
+
 size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // workspace: 10 complex fields, 3 real fields, reduction partials and results
@@ -312,14 +394,7 @@ fse_status ground_state(fse_plan* P, void* psi_v, void* ws, const fse_gs_opts& o
   G.st = P->stream;
   G.N = (long long)P->nx * P->ny * P->nz;
   G.blocks = (int)std::min<long long>(kGsBlocks, (G.N + 255) / 256);
-  G.g.nx = P->nx;
-  G.g.ny = P->ny;
-  G.g.nz = P->nz;
-  for (int j = 0; j < 3; ++j) {
-    G.g.lo[j] = j < P->dim ? P->p.lo[j] : 0.0;
-    G.g.h[j] = j < P->dim ? P->h[j] : 0.0;
-    G.g.dk[j] = j < P->dim ? 2 * kPi / (P->p.hi[j] - P->p.lo[j]) : 0.0;
-  }
+  G.g = gs_grid(P);
   C** cp[10] = {&G.phin, &G.r, &G.rh, &G.p, &G.v, &G.s, &G.t, &G.t1, &G.t2, &G.t3};
   for (int i = 0; i < 10; ++i) *cp[i] = reinterpret_cast<C*>(base + L.cplx[i]);
   G.W = reinterpret_cast<Real*>(base + L.real[0]);
@@ -435,4 +510,14 @@ extern "C" fse_status fse_ground_state(fse_plan_t P, void* psi, void* workspace,
     return fail(P, FSE_ERR_INVALID, "ground state: bad options");
   return P->prec == FSE_F32 ? ground_state<float>(P, psi, workspace, *opts, info)
                             : ground_state<double>(P, psi, workspace, *opts, info);
+}
+
+extern "C" fse_status fse_shift_kick(fse_plan_t P, void* psi, const double* x0, const double* k) {
+  if (!P || !psi) return FSE_ERR_INVALID;
+  if (!P->ws || !P->precomputed) return fail(P, FSE_ERR_INVALID, "fse_kernel_precompute has not run");
+  if (reinterpret_cast<uintptr_t>(psi) % P->csize != 0) return fail(P, FSE_ERR_INVALID, "misaligned buffer");
+  for (int j = 0; j < P->dim; ++j)
+    if ((x0 && !std::isfinite(x0[j])) || (k && !std::isfinite(k[j])))
+      return fail(P, FSE_ERR_INVALID, "shift or kick not finite");
+  return P->prec == FSE_F32 ? shift_kick<float>(P, psi, x0, k) : shift_kick<double>(P, psi, x0, k);
 }

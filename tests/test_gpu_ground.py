@@ -76,3 +76,25 @@ def test_float32_ground_state_energy(lib):
     e_ref = O.observables(ref, p, 0.0)["energy"]
     e_gpu = plan.observables(x, 0.0)["energy"]
     assert abs(e_gpu - e_ref) < 1e-5 * abs(e_ref), (e_gpu, e_ref, info)
+
+
+def test_shifted_ground_state_dynamics_match_oracle(lib):
+    """Eq. ini_dyn: a ground state shifted by x0 and kicked by v0 (0.8, 0.5), then
+    TS2-GauSum steps (the paper's shifted-data runs, here at a reduced size)."""
+    d = dict(dim=2, n=(64, 64), lo=(-8.0, -8.0), hi=(8.0, 8.0), s=0.75, omega=0.0, beta=50.0, lam=0.0,
+             kernel="coulomb", gamma=(1.0, 1.0), dt=1e-3, prec="f64")
+    p = O.params(d)
+    phig, *_ = O.ground_state(_guess(p), p, 0.1, 400, tol=1e-8, inner_tol=1e-12)
+    x0, k = (1.0, 1.0), (0.8, 0.5)
+    ref0 = O.shift_kick(phig, p, x0=x0, k=k)
+    plan = lib.Plan(d)
+    x = plan.to_device(phig)
+    plan.shift_kick(x, x0, k)
+    torch.cuda.synchronize()
+    got0 = x.cpu().numpy()
+    assert np.max(np.abs(got0 - ref0)) < 1e-12 * np.max(np.abs(ref0))
+    ref = O.evolve(ref0, p, 0.0, 20)
+    plan.step(x, 0.0, 20)
+    torch.cuda.synchronize()
+    got = x.cpu().numpy()
+    assert np.linalg.norm((got - ref).ravel()) / np.linalg.norm(ref.ravel()) < 1e-11

@@ -88,3 +88,23 @@ def test_nonlinear_ground_state_is_stationary(s, omega, kernel):
     # the energy of the ground state is below that of the starting state
     g0 = _gauss(p) / math.sqrt(O.mass(_gauss(p), p))
     assert O.observables(phi, p, 0.0)["energy"] < O.observables(g0, p, 0.0)["energy"]
+
+
+def test_shift_kick():
+    """Eq. ini_dyn: a grid-multiple shift is np.roll exactly; a fractional shift of a
+    Gaussian is the shifted Gaussian; the kick multiplies by exp(i k.x)."""
+    p = O.Params(dim=2, n=(32, 24), lo=(-8.0, -6.0), hi=(8.0, 6.0), kernel="none")
+    rng = np.random.default_rng(4)
+    phi = rng.standard_normal(p.shape()) + 1j * rng.standard_normal(p.shape())
+    h = O.mesh_size(p)
+    got = O.shift_kick(phi, p, x0=(3 * h[0], -2 * h[1]))
+    assert np.max(np.abs(got - np.roll(phi, (-2, 3), axis=(0, 1)))) < 1e-12
+    p = O.Params(dim=2, n=(64, 48), lo=(-8.0, -6.0), hi=(8.0, 6.0), kernel="none")   # band-limited Gaussian
+    X = O.coords(p)
+    g = np.exp(-((X[0] - 0.4) ** 2 + (X[1] + 0.3) ** 2))
+    x0 = (0.37, -0.21)
+    ex = np.exp(-((X[0] - 0.4 - x0[0]) ** 2 + (X[1] + 0.3 - x0[1]) ** 2))
+    assert np.max(np.abs(O.shift_kick(g, p, x0=x0) - ex)) < 1e-12
+    k = (0.8, 0.5)
+    got = O.shift_kick(g, p, k=k)
+    assert np.max(np.abs(got - g * np.exp(1j * (0.8 * X[0] + 0.5 * X[1])))) < 1e-15
