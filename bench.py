@@ -277,6 +277,7 @@ def main():
     ap.add_argument("--oracle-steps", type=int, default=1)
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--gs-steps", type=int, default=20)
+    ap.add_argument("--configs", type=int, default=1, help="1: also time the other configurations")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -418,6 +419,48 @@ def main():
                    "sizes": sorted({r["n"][0] for r in runs})}
         del bt, xs
 
+    # the other configurations: steps/s of the 2D Coulomb (float64) and 128^3
+    # dipolar (float32) runs, and forward + adjoint steps/s of the gradient run
+    configs = None
+    if args.configs:
+        configs = {}
+        for name in ("2d_coulomb_128", "3d_dipolar_128"):
+            dc = I.workload(name)
+            pc = fse.Plan(dc, stream=stream, device=dev)
+            xc = pc.to_device(I.psi0(name))
+            pc.step(xc, 0.0, 5)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pc.step(xc, 5 * dc["dt"], dc["steps"])
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            configs[name] = {"split_steps_per_s": dc["steps"] / (e0.elapsed_time(e1) / 1000.0),
+                             "steps": dc["steps"], "dtype": dc["prec"]}
+            del pc, xc
+        from paper_1512_03210_gb300 import autograd as AG
+        da = I.workload("adjoint_2d_256")
+        pa = fse.Plan(da, stream=stream, device=dev)
+        gam = torch.tensor(I.adjoint_gammas(da["steps"]), dtype=torch.float64)
+        tgt = pa.to_device(I.adjoint_target(da))
+        cell = float(np.prod([(da["hi"][j] - da["lo"][j]) / da["n"][j] for j in range(2)]))
+
+        def fwd_bwd():
+            x0 = pa.to_device(I.psi0("adjoint_2d_256")).requires_grad_(True)
+            g = gam.clone().requires_grad_(True)
+            J = AG.overlap_objective(AG.evolve(pa, x0, g), tgt, cell)
+            J.backward()
+            return J
+        fwd_bwd()
+        torch.cuda.synchronize(dev)
+        t0a = time.perf_counter()
+        fwd_bwd()
+        torch.cuda.synchronize(dev)
+        sa = time.perf_counter() - t0a
+        configs["adjoint_2d_256"] = {"gradient_steps_per_s": da["steps"] / sa, "steps": da["steps"],
+                                     "dtype": da["prec"],
+                                     "note": "forward with sqrt(T) checkpoints, recomputation and adjoint; host-timed"}
+        del pa
+
     # GF-GauSum ground state (Section 3.2): normalised gradient-flow steps, each a
     # BiCGStab solve through the library's FFT passes (the call synchronises)
     gs = None
@@ -460,7 +503,7 @@ def main():
         "grid_point_steps_per_s": value * 256 ** 3,
         "model_bytes_per_step": step_bytes,
         "step_roofline_frac": step_bytes * value / world / 1e9 / peak,
-        "roofline": roofline, "kernels": kernels, "f64": f64, "e2e": e2e, "batched_2d": batched, "ground_state": gs,
+        "roofline": roofline, "kernels": kernels, "f64": f64, "e2e": e2e, "batched_2d": batched, "ground_state": gs, "configs": configs,
         "cpu_baseline": cb, "gpu_launches": launches, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
