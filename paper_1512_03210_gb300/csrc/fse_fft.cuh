@@ -216,6 +216,27 @@ __device__ __forceinline__ float norm_err(float c, float s) {
 
 // v times twiddle m of the table (conjugated for the inverse transform); the
 // table is in global memory, or in shared memory when TWS is set.
+template <bool EXACT, bool TWS, typename C>
+__device__ __forceinline__ void twiddle_load(const C* __restrict__ tw, int m, C& w, C& l) {
+  w = TWS ? tw[2 * m] : __ldg(&tw[2 * m]);
+  if constexpr (EXACT && sizeof(C) == 8) l = TWS ? tw[2 * m + 1] : __ldg(&tw[2 * m + 1]);
+  else l = w;
+}
+template <int DIR, bool EXACT, typename C>
+__device__ __forceinline__ C twiddle_apply(C v, C w, C l) {
+  if constexpr (EXACT && sizeof(C) == 8) {
+    if constexpr (DIR < 0) {
+      const float lr = v.x * l.x - v.y * l.y, li = v.x * l.y + v.y * l.x;
+      return mk(fmaf(v.x, w.x, fmaf(-v.y, w.y, lr)), fmaf(v.x, w.y, fmaf(v.y, w.x, li)));
+    } else {
+      const float lr = v.x * l.x + v.y * l.y, li = v.y * l.x - v.x * l.y;
+      return mk(fmaf(v.x, w.x, fmaf(v.y, w.y, lr)), fmaf(-v.x, w.y, fmaf(v.y, w.x, li)));
+    }
+  } else {
+    return DIR < 0 ? cmul(v, w) : cmulc(v, w);
+  }
+}
+
 template <int DIR, bool EXACT, bool TWS = false, typename C>
 __device__ __forceinline__ C twiddle_mul(C v, const C* __restrict__ tw, int m) {
   const C w = TWS ? tw[2 * m] : __ldg(&tw[2 * m]);
@@ -305,14 +326,16 @@ __device__ __forceinline__ void fft_tile(C* buf, const C* __restrict__ tw) {
 }
 
 // ---------------------------------------------------------------------------
-// Register-staged Stockham for column tiles. Each thread owns E elements of the
-// tile in registers (E a multiple of every radix of the plan). Pass p works on
-// items (c, j), j < N/R_p, item i of thread t being w = t + i NT, c = w % NCOL,
-// j = w / NCOL; its inputs are at positions j + r N/R_p and its outputs at
-// (j / Ns) Ns R_p + j % Ns + r Ns. The first pass's inputs come from global
-// memory and the last pass's outputs (positions j + r N/R_last) stay in
-// registers, so a transform of P passes makes P - 1 exchanges through shared
-// memory instead of P + 1.
+// Register-staged Stockham for column tiles. A tile holds NCP groups of CW
+// adjacent columns (CW = 2 on the float path: one 16-byte access moves a row of
+// both columns, and the two share every twiddle). Each thread owns E elements
+// in registers; pass p works on items (g, j), j < N/R_p, item i of thread t
+// being w = t + i NT, g = w % NCP, j = w / NCP, and element (item i, column q,
+// radix index r) is v[(i CW + q) R_p + r]. An item's inputs are at positions
+// j + r N/R_p and its outputs at (j / Ns) Ns R_p + j % Ns + r Ns. The first
+// pass's inputs come from global memory and the last pass's outputs
+// (positions j + r N/R_last) stay in registers, so a transform of P passes
+// makes P - 1 exchanges through the shared tile (leading dimension LDS).
 // ---------------------------------------------------------------------------
 __host__ __device__ constexpr int plan_lcm(int N) {
   RadixPlan p = radix_plan(N);
@@ -324,52 +347,75 @@ __host__ __device__ constexpr int plan_lcm(int N) {
   }
   return two * (three ? 3 : 1);
 }
-// elements per thread and threads per tile of NCOL lines of length N
-__host__ __device__ constexpr int reg_elems(int N, int ncol) {
-  int e = plan_lcm(N);
+// elements per thread and threads per tile of NCOL lines of length N, CW columns per item
+__host__ __device__ constexpr int reg_elems(int N, int ncol, int cw = 1) {
+  int e = plan_lcm(N) * cw;
   while (N * ncol / e > 512) e *= 2;
   return e;
 }
-__host__ __device__ constexpr int reg_threads(int N, int ncol) { return N * ncol / reg_elems(N, ncol); }
+__host__ __device__ constexpr int reg_threads(int N, int ncol, int cw = 1) { return N * ncol / reg_elems(N, ncol, cw); }
 
-template <typename C, int N, int NCOL, int NT, int E, int DIR, bool EXACT, int R, int NS, bool TWS>
+__device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+__device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  a = make_float2(t.x, t.y);
+  b = make_float2(t.z, t.w);
+}
+
+template <typename C, int N, int NCP, int CW, int NT, int E, int DIR, bool EXACT, int R, int NS, bool TWS>
 __device__ __forceinline__ void regs_pass(C (&v)[E], const C* __restrict__ tw) {
-  constexpr int I = E / R;
+  constexpr int I = E / (R * CW);
   const int tid = threadIdx.x;
 #pragma unroll
   for (int i = 0; i < I; ++i) {
-    const int j = (tid + i * NT) / NCOL;
+    const int j = (tid + i * NT) / NCP;
     if constexpr (NS > 1) {
       const int k = j % NS;
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[i * R + r] = twiddle_mul<DIR, EXACT, TWS>(v[i * R + r], tw, (k * r) * (N / (NS * R)));
+      for (int r = 1; r < R; ++r) {
+        C w, l;
+        twiddle_load<EXACT, TWS>(tw, (k * r) * (N / (NS * R)), w, l);
+#pragma unroll
+        for (int q = 0; q < CW; ++q) v[(i * CW + q) * R + r] = twiddle_apply<DIR, EXACT>(v[(i * CW + q) * R + r], w, l);
+      }
     }
-    dft<R, DIR, EXACT>(&v[i * R]);
+#pragma unroll
+    for (int q = 0; q < CW; ++q) dft<R, DIR, EXACT>(&v[(i * CW + q) * R]);
   }
 }
 
-template <typename C, int N, int NCOL, int NT, int E, int R, int NS>
+template <typename C, int N, int NCP, int CW, int NT, int E, int R, int NS, int LDS>
 __device__ __forceinline__ void regs_to_smem(const C (&v)[E], C* buf) {
-  constexpr int I = E / R, LDS = NCOL + 1;
+  constexpr int I = E / (R * CW);
   const int tid = threadIdx.x;
 #pragma unroll
   for (int i = 0; i < I; ++i) {
-    const int w = tid + i * NT, c = w % NCOL, j = w / NCOL;
+    const int w = tid + i * NT, g = w % NCP, j = w / NCP;
     const int base = (j / NS) * NS * R + j % NS;
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[(base + r * NS) * LDS + c] = v[i * R + r];
+    for (int r = 0; r < R; ++r) {
+      C* p = &buf[(base + r * NS) * LDS + g * CW];
+      if constexpr (CW == 2) st_pair(p, v[(i * 2) * R + r], v[(i * 2 + 1) * R + r]);
+      else *p = v[i * R + r];
+    }
   }
 }
 
-template <typename C, int N, int NCOL, int NT, int E, int R>
+template <typename C, int N, int NCP, int CW, int NT, int E, int R, int LDS>
 __device__ __forceinline__ void smem_to_regs(C (&v)[E], const C* buf) {
-  constexpr int I = E / R, LDS = NCOL + 1;
+  constexpr int I = E / (R * CW);
   const int tid = threadIdx.x;
 #pragma unroll
   for (int i = 0; i < I; ++i) {
-    const int w = tid + i * NT, c = w % NCOL, j = w / NCOL;
+    const int w = tid + i * NT, g = w % NCP, j = w / NCP;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[i * R + r] = buf[(j + r * (N / R)) * LDS + c];
+    for (int r = 0; r < R; ++r) {
+      const C* p = &buf[(j + r * (N / R)) * LDS + g * CW];
+      if constexpr (CW == 2) ld_pair(p, v[(i * 2) * R + r], v[(i * 2 + 1) * R + r]);
+      else v[i * R + r] = *p;
+    }
   }
 }
 
@@ -392,19 +438,19 @@ __host__ __device__ constexpr int plan_radix(int p) {
 // radices are taken in reverse order: a transform whose inputs are the outputs
 // of a forward-order transform (positions j + r N/R_last) then starts without an
 // exchange, since its first radix is that transform's last one.
-template <typename C, int N, int NCOL, int NT, int E, int DIR, bool EXACT, int PASS, int NS, bool REV = false,
-          bool TWS = false>
+template <typename C, int N, int NCP, int CW, int NT, int E, int LDS, int DIR, bool EXACT, int PASS, int NS,
+          bool REV = false, bool TWS = false>
 __device__ __forceinline__ void regs_fft(C (&v)[E], C* buf, const C* __restrict__ tw) {
   constexpr int NP = radix_plan(N).npass;
   constexpr int R = plan_radix<N, REV>(PASS);
-  regs_pass<C, N, NCOL, NT, E, DIR, EXACT, R, NS, TWS>(v, tw);
+  regs_pass<C, N, NCP, CW, NT, E, DIR, EXACT, R, NS, TWS>(v, tw);
   if constexpr (PASS + 1 < NP) {
     constexpr int R2 = plan_radix<N, REV>(PASS + 1);
-    regs_to_smem<C, N, NCOL, NT, E, R, NS>(v, buf);
+    regs_to_smem<C, N, NCP, CW, NT, E, R, NS, LDS>(v, buf);
     __syncthreads();
-    smem_to_regs<C, N, NCOL, NT, E, R2>(v, buf);
+    smem_to_regs<C, N, NCP, CW, NT, E, R2, LDS>(v, buf);
     __syncthreads();
-    regs_fft<C, N, NCOL, NT, E, DIR, EXACT, PASS + 1, NS * R, REV, TWS>(v, buf, tw);
+    regs_fft<C, N, NCP, CW, NT, E, LDS, DIR, EXACT, PASS + 1, NS * R, REV, TWS>(v, buf, tw);
   }
 }
 

@@ -141,13 +141,18 @@ template <typename Real, int N>
 struct ColCfg {
   typedef typename Cplx<Real>::T C;
   static constexpr int NCOL = col_ncol(N, sizeof(C));
-  static constexpr int E = reg_elems(N, NCOL);
-  static constexpr int NT = reg_threads(N, NCOL);
+  // float path, power-of-two plans (radices up to 8): items of two adjacent
+  // columns (16-byte row accesses, shared twiddles); otherwise one column
+  static constexpr int CW = (sizeof(C) == 8 && plan_lcm(N) <= 8 && NCOL % 2 == 0) ? 2 : 1;
+  static constexpr int NCP = NCOL / CW;
+  static constexpr int LDS = CW == 2 ? NCOL + 2 : NCOL + 1;  // even for 16-byte pairs
+  static constexpr int E = reg_elems(N, NCOL, CW);
+  static constexpr int NT = reg_threads(N, NCOL, CW);
   static constexpr int R0 = radix_plan(N).r[0];
   static constexpr int RL = radix_plan(N).r[radix_plan(N).npass - 1];
   static constexpr int MINB = (sizeof(C) == 8 && E > 16) ? (512 / NT > 0 ? 512 / NT : 1) : minb_for(NT, sizeof(C));
   // exchange tile, then (kernel-transform variant) the block's C^ values on |p| = 0..N/2
-  static constexpr size_t TILE_BYTES = sizeof(C) * (size_t)N * (NCOL + 1);
+  static constexpr size_t TILE_BYTES = sizeof(C) * (size_t)N * LDS;
   __host__ __device__ static constexpr size_t tile_bytes() { return TILE_BYTES; }
   __host__ __device__ static constexpr size_t chat_bytes() { return sizeof(Real) * (size_t)(N / 2 + 1) * NCOL; }
   // copy of the twiddle table (pairs, 2 N entries), after the tile and C^ values
@@ -168,7 +173,8 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
                                              const typename Cplx<Real>::T* __restrict__ tw, int bid) {
   typedef ColCfg<Real, N> K;
   typedef typename K::C C;
-  constexpr int NCOL = K::NCOL, NT = K::NT, E = K::E, R0 = K::R0, RL = K::RL;
+  constexpr int NCOL = K::NCOL, NCP = K::NCP, CW = K::CW, LDS = K::LDS, NT = K::NT, E = K::E;
+  constexpr int R0 = K::R0, RL = K::RL;
   // forward . multiplier . inverse variants whose radix plan reads the same
   // reversed (all radix 8, e.g. N = 512) run the inverse straight on the
   // forward's outputs as they sit in registers (positions j + r N/RL); other
@@ -185,8 +191,8 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int tid = threadIdx.x;
-  static_assert(NT % NCOL == 0, "a thread keeps one column of the tile");
-  const int cme = tid % NCOL;  // this thread's column of the tile
+  static_assert(NT % NCP == 0, "a thread keeps one column group of the tile");
+  const int cg = tid % NCP;  // this thread's columns of the tile: cg CW + q, q < CW
   // only passes over R2C bins (ncols = nx + 1) have tail tiles; they come
   // first in the grid, so that they overlap the full tiles
   constexpr bool TAILS = (VAR == COL_PADF || VAR == COL_CROPI || VAR == COL_KHAT);
@@ -216,11 +222,21 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
     px = 0;
     return false;
   };
-  int my_plane = plane, my_px = c0 + cme;
-  bool my_ok = my_px < a.ncols;
-  if (gather) my_ok = col_of(cme, my_plane, my_px);
-  // row r of this thread's column is colp[r * line_stride + cme]
-  C* colp = reinterpret_cast<C*>(a.data) + (long long)my_plane * a.plane_stride + (my_px - cme);
+  // this thread's columns: plane, x index, validity and base pointer (row r of
+  // column q is colp[q][r * line_stride])
+  int my_plane[CW], my_px[CW];
+  bool my_ok[CW];
+  C* colp[CW];
+#pragma unroll
+  for (int q = 0; q < CW; ++q) {
+    my_ok[q] = col_of(cg * CW + q, my_plane[q], my_px[q]);
+    colp[q] = reinterpret_cast<C*>(a.data) + (long long)my_plane[q] * a.plane_stride + my_px[q];
+  }
+  // both columns of a pair side by side in memory, 16-byte aligned: one access per row
+  bool vec = false;
+  if constexpr (CW == 2)
+    vec = !gather && my_ok[0] && my_ok[1] && (reinterpret_cast<uintptr_t>(colp[0]) % 16 == 0) &&
+          (a.line_stride % 2 == 0);
   C v[E];
   Real* sC = reinterpret_cast<Real*>(smem_raw + K::TILE_BYTES);
   constexpr bool TWS = K::tws(VAR);
@@ -264,15 +280,27 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
 
   // inputs of the first pass straight from global memory
 #pragma unroll
-  for (int i = 0; i < E / R0; ++i) {
-    const int j = (tid + i * NT) / NCOL;
+  for (int i = 0; i < E / (R0 * CW); ++i) {
+    const int j = (tid + i * NT) / NCP;
 #pragma unroll
     for (int r = 0; r < R0; ++r) {
       const int row = j + r * (N / R0);
+      C* dst[CW];
+#pragma unroll
+      for (int q = 0; q < CW; ++q) dst[q] = &v[(i * CW + q) * R0 + r];
       if (HALF_IN && 2 * r >= R0) {
-        v[i * R0 + r] = mk(Real(0), Real(0));  // rows >= N/2 of a zero-padded line
+#pragma unroll
+        for (int q = 0; q < CW; ++q) *dst[q] = mk(Real(0), Real(0));  // rows >= N/2 of a zero-padded line
+      } else if constexpr (CW == 2) {
+        if (row < a.n_load && vec) {
+          ld_pair(&colp[0][(long long)row * a.line_stride], *dst[0], *dst[1]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < CW; ++q)
+            *dst[q] = (row < a.n_load && my_ok[q]) ? colp[q][(long long)row * a.line_stride] : mk(Real(0), Real(0));
+        }
       } else {
-        v[i * R0 + r] = (row < a.n_load && my_ok) ? colp[(long long)row * a.line_stride + cme] : mk(Real(0), Real(0));
+        *dst[0] = (row < a.n_load && my_ok[0]) ? colp[0][(long long)row * a.line_stride] : mk(Real(0), Real(0));
       }
     }
   }
@@ -284,81 +312,108 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
     if constexpr (radix_plan(N).npass < 2) __syncthreads();
   }
   if constexpr (VAR == COL_FWD || VAR == COL_INV || VAR == COL_PADF || VAR == COL_CROPI) {
-    regs_fft<C, N, NCOL, NT, E, DIR1, EXACT, 0, 1, false, TWS>(v, buf, tw);
+    regs_fft<C, N, NCP, CW, NT, E, LDS, DIR1, EXACT, 0, 1, false, TWS>(v, buf, tw);
   } else {
-    regs_fft<C, N, NCOL, NT, E, -1, EXACT, 0, 1, false, TWS>(v, buf, tw);
+    regs_fft<C, N, NCP, CW, NT, E, LDS, -1, EXACT, 0, 1, false, TWS>(v, buf, tw);
     // spectral multiplier on the outputs (row = frequency index along the axis)
     if constexpr (VAR == COL_KIN) {
       // kinetic phase exp(-i f theta_k) from the plan's octant table, indexed by
       // |p_x| (column), |p_plane| and |p_row| (row = frequency index along the axis)
-      const C* tab = reinterpret_cast<const C*>(m.kin) + (m.lp ? (long long)abs(wrap_index(my_plane, m.lp)) * m.kin_sp : 0);
-      const Real sc = Real(m.scale);
-      const int ax = abs(wrap_index(min(my_px, m.lx - 1), m.lx));
+      const C* tab[CW];
+      int ax[CW];
 #pragma unroll
-      for (int i = 0; i < E / RL; ++i) {
-        const int j = (tid + i * NT) / NCOL;
+      for (int q = 0; q < CW; ++q) {
+        tab[q] = reinterpret_cast<const C*>(m.kin) + (m.lp ? (long long)abs(wrap_index(my_plane[q], m.lp)) * m.kin_sp : 0);
+        ax[q] = abs(wrap_index(min(my_px[q], m.lx - 1), m.lx));
+      }
+      const Real sc = Real(m.scale);
+#pragma unroll
+      for (int i = 0; i < E / (RL * CW); ++i) {
+        const int j = (tid + i * NT) / NCP;
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
           const int row = j + r * (N / RL);
-          const C t = my_ok ? __ldg(&tab[(long long)abs(wrap_index(row, m.lr)) * m.kin_sr + ax]) : mk(Real(1), Real(0));
-          const C x = unit_mul(v[i * RL + r], t.x, t.y, m.conj != 0);
-          if constexpr (FUSED) v[i * RL + r] = mk(sc * x.x, sc * x.y);
-          else buf[row * (NCOL + 1) + cme] = mk(sc * x.x, sc * x.y);
+          const long long ro = (long long)abs(wrap_index(row, m.lr)) * m.kin_sr;
+#pragma unroll
+          for (int q = 0; q < CW; ++q) {
+            const C t = my_ok[q] ? __ldg(&tab[q][ro + ax[q]]) : mk(Real(1), Real(0));
+            const C x = unit_mul(v[(i * CW + q) * RL + r], t.x, t.y, m.conj != 0);
+            if constexpr (FUSED) v[(i * CW + q) * RL + r] = mk(sc * x.x, sc * x.y);
+            else buf[row * LDS + cg * CW + q] = mk(sc * x.x, sc * x.y);
+          }
         }
       }
     } else {
-      // kernel transform on the padded grid: f = a0 C^ (Coulomb) or a0 + (k^T Q k) C^ (3D DDI);
+      // kernel transform on the padded grid: f = a0 C^ (Coulomb) or a0 + (k^T Q k) C^ (DDI);
       // the column (x, an R2C bin 0..nx) and plane factors are fixed per thread
       cp_async_wait_all();
       __syncthreads();
-      const Real kp = m.lp ? Real(m.dkp) * Real(wrap_index(my_plane, m.lp)) : Real(0);
-      const Real kpo = (m.lp && 2 * my_plane == m.lp) ? Real(0) : kp;
       const bool ddi = m.mode == MUL_DDI;
-      const Real kx = Real(m.dkx) * Real(my_px);
-      const Real kxo = (2 * my_px == m.lx) ? Real(0) : kx;
-      // q(k) = A + B kr + q2 kr^2 (kr replaced by 0 in B at the Nyquist row)
-      const Real Aq = Real(m.q[0]) * kx * kx + Real(m.q[1]) * kp * kp + Real(m.q[3]) * kxo * kpo;
-      const Real Bq = Real(m.q[4]) * kxo + Real(m.q[5]) * kpo;
+      Real Aq[CW], Bq[CW];
 #pragma unroll
-      for (int i = 0; i < E / RL; ++i) {
-        const int j = (tid + i * NT) / NCOL;
+      for (int q = 0; q < CW; ++q) {
+        const Real kp = m.lp ? Real(m.dkp) * Real(wrap_index(my_plane[q], m.lp)) : Real(0);
+        const Real kpo = (m.lp && 2 * my_plane[q] == m.lp) ? Real(0) : kp;
+        const Real kx = Real(m.dkx) * Real(my_px[q]);
+        const Real kxo = (2 * my_px[q] == m.lx) ? Real(0) : kx;
+        // q(k) = A + B kr + q2 kr^2 (kr replaced by 0 in B at the Nyquist row)
+        Aq[q] = Real(m.q[0]) * kx * kx + Real(m.q[1]) * kp * kp + Real(m.q[3]) * kxo * kpo;
+        Bq[q] = Real(m.q[4]) * kxo + Real(m.q[5]) * kpo;
+      }
+#pragma unroll
+      for (int i = 0; i < E / (RL * CW); ++i) {
+        const int j = (tid + i * NT) / NCP;
 #pragma unroll
         for (int r = 0; r < RL; ++r) {
           const int row = j + r * (N / RL);
           const int pr = wrap_index(row, m.lr);
-          const Real cv = sC[abs(pr) * NCOL + cme];
-          Real f;
-          if (ddi) {
-            const Real kr = Real(m.dkr) * Real(pr);
-            const Real kro = (2 * row == m.lr) ? Real(0) : kr;
-            const Real qf = Aq + Bq * kro + Real(m.q[2]) * kr * kr;
-            f = Real(m.a0) + qf * cv;
-          } else {
-            f = Real(m.a0) * cv;
+          const Real kr = Real(m.dkr) * Real(pr);
+          const Real kro = (2 * row == m.lr) ? Real(0) : kr;
+#pragma unroll
+          for (int q = 0; q < CW; ++q) {
+            const Real cv = sC[abs(pr) * NCOL + cg * CW + q];
+            Real f;
+            if (ddi) {
+              const Real qf = Aq[q] + Bq[q] * kro + Real(m.q[2]) * kr * kr;
+              f = Real(m.a0) + qf * cv;
+            } else {
+              f = Real(m.a0) * cv;
+            }
+            const C x = v[(i * CW + q) * RL + r];
+            if constexpr (FUSED) v[(i * CW + q) * RL + r] = mk(f * x.x, f * x.y);
+            else buf[row * LDS + cg * CW + q] = mk(f * x.x, f * x.y);
           }
-          const C x = v[i * RL + r];
-          if constexpr (FUSED) v[i * RL + r] = mk(f * x.x, f * x.y);
-          else buf[row * (NCOL + 1) + cme] = mk(f * x.x, f * x.y);
         }
       }
     }
     if constexpr (!FUSED) {
       // (the forward's last exchange ended with a barrier, so buf was free)
       __syncthreads();
-      smem_to_regs<C, N, NCOL, NT, E, R0>(v, buf);
+      smem_to_regs<C, N, NCP, CW, NT, E, R0, LDS>(v, buf);
       __syncthreads();
     }
-    regs_fft<C, N, NCOL, NT, E, +1, EXACT, 0, 1, FUSED, TWS>(v, buf, tw);
+    regs_fft<C, N, NCP, CW, NT, E, LDS, +1, EXACT, 0, 1, FUSED, TWS>(v, buf, tw);
   }
   // outputs of the last pass to global memory (rows >= n_store cropped)
 #pragma unroll
-  for (int i = 0; i < E / RF; ++i) {
-    const int j = (tid + i * NT) / NCOL;
+  for (int i = 0; i < E / (RF * CW); ++i) {
+    const int j = (tid + i * NT) / NCP;
 #pragma unroll
     for (int r = 0; r < RF; ++r) {
       const int row = j + r * (N / RF);
       if (HALF_OUT && 2 * r >= RF) continue;  // rows >= N/2 are cropped
-      if (row < a.n_store && my_ok) colp[(long long)row * a.line_stride + cme] = v[i * RF + r];
+      if (row >= a.n_store) continue;
+      if constexpr (CW == 2) {
+        if (vec) {
+          st_pair(&colp[0][(long long)row * a.line_stride], v[(i * 2) * RF + r], v[(i * 2 + 1) * RF + r]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < CW; ++q)
+            if (my_ok[q]) colp[q][(long long)row * a.line_stride] = v[(i * CW + q) * RF + r];
+        }
+      } else {
+        if (my_ok[0]) colp[0][(long long)row * a.line_stride] = v[i * RF + r];
+      }
     }
   }
 }
