@@ -214,12 +214,13 @@ __device__ __forceinline__ float norm_err(float c, float s) {
   return ((pa - 1.0f) + pb) + (ea + eb);
 }
 
-// v times twiddle m of the table (conjugated for the inverse transform); the
-// table is in global memory, or in shared memory when TWS is set.
-template <bool EXACT, bool TWS, typename C>
+// Twiddle m of the table: rounded pair w and its remainder l (EXACT float path;
+// otherwise l = w unused). The transforms multiply with twiddle_apply,
+// conjugated for the inverse transform.
+template <bool EXACT, typename C>
 __device__ __forceinline__ void twiddle_load(const C* __restrict__ tw, int m, C& w, C& l) {
-  w = TWS ? tw[2 * m] : __ldg(&tw[2 * m]);
-  if constexpr (EXACT && sizeof(C) == 8) l = TWS ? tw[2 * m + 1] : __ldg(&tw[2 * m + 1]);
+  w = __ldg(&tw[2 * m]);
+  if constexpr (EXACT && sizeof(C) == 8) l = __ldg(&tw[2 * m + 1]);
   else l = w;
 }
 template <int DIR, bool EXACT, typename C>
@@ -237,21 +238,12 @@ __device__ __forceinline__ C twiddle_apply(C v, C w, C l) {
   }
 }
 
-template <int DIR, bool EXACT, bool TWS = false, typename C>
+// v times twiddle m of the table (conjugated for the inverse transform).
+template <int DIR, bool EXACT, typename C>
 __device__ __forceinline__ C twiddle_mul(C v, const C* __restrict__ tw, int m) {
-  const C w = TWS ? tw[2 * m] : __ldg(&tw[2 * m]);
-  if constexpr (EXACT && sizeof(C) == 8) {
-    const C l = TWS ? tw[2 * m + 1] : __ldg(&tw[2 * m + 1]);
-    if constexpr (DIR < 0) {
-      const float lr = v.x * l.x - v.y * l.y, li = v.x * l.y + v.y * l.x;
-      return mk(fmaf(v.x, w.x, fmaf(-v.y, w.y, lr)), fmaf(v.x, w.y, fmaf(v.y, w.x, li)));
-    } else {
-      const float lr = v.x * l.x + v.y * l.y, li = v.y * l.x - v.x * l.y;
-      return mk(fmaf(v.x, w.x, fmaf(v.y, w.y, lr)), fmaf(-v.x, w.y, fmaf(v.y, w.x, li)));
-    }
-  } else {
-    return DIR < 0 ? cmul(v, w) : cmulc(v, w);
-  }
+  C w, l;
+  twiddle_load<EXACT>(tw, m, w, l);
+  return twiddle_apply<DIR, EXACT>(v, w, l);
 }
 
 // v times the float pair (c, s) of a unit-modulus factor, with the pair's
@@ -364,7 +356,7 @@ __device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
   b = make_float2(t.z, t.w);
 }
 
-template <typename C, int N, int NCP, int CW, int NT, int E, int DIR, bool EXACT, int R, int NS, bool TWS>
+template <typename C, int N, int NCP, int CW, int NT, int E, int DIR, bool EXACT, int R, int NS>
 __device__ __forceinline__ void regs_pass(C (&v)[E], const C* __restrict__ tw) {
   constexpr int I = E / (R * CW);
   const int tid = threadIdx.x;
@@ -376,7 +368,7 @@ __device__ __forceinline__ void regs_pass(C (&v)[E], const C* __restrict__ tw) {
 #pragma unroll
       for (int r = 1; r < R; ++r) {
         C w, l;
-        twiddle_load<EXACT, TWS>(tw, (k * r) * (N / (NS * R)), w, l);
+        twiddle_load<EXACT>(tw, (k * r) * (N / (NS * R)), w, l);
 #pragma unroll
         for (int q = 0; q < CW; ++q) v[(i * CW + q) * R + r] = twiddle_apply<DIR, EXACT>(v[(i * CW + q) * R + r], w, l);
       }
@@ -439,18 +431,18 @@ __host__ __device__ constexpr int plan_radix(int p) {
 // of a forward-order transform (positions j + r N/R_last) then starts without an
 // exchange, since its first radix is that transform's last one.
 template <typename C, int N, int NCP, int CW, int NT, int E, int LDS, int DIR, bool EXACT, int PASS, int NS,
-          bool REV = false, bool TWS = false>
+          bool REV = false>
 __device__ __forceinline__ void regs_fft(C (&v)[E], C* buf, const C* __restrict__ tw) {
   constexpr int NP = radix_plan(N).npass;
   constexpr int R = plan_radix<N, REV>(PASS);
-  regs_pass<C, N, NCP, CW, NT, E, DIR, EXACT, R, NS, TWS>(v, tw);
+  regs_pass<C, N, NCP, CW, NT, E, DIR, EXACT, R, NS>(v, tw);
   if constexpr (PASS + 1 < NP) {
     constexpr int R2 = plan_radix<N, REV>(PASS + 1);
     regs_to_smem<C, N, NCP, CW, NT, E, R, NS, LDS>(v, buf);
     __syncthreads();
     smem_to_regs<C, N, NCP, CW, NT, E, R2, LDS>(v, buf);
     __syncthreads();
-    regs_fft<C, N, NCP, CW, NT, E, LDS, DIR, EXACT, PASS + 1, NS * R, REV, TWS>(v, buf, tw);
+    regs_fft<C, N, NCP, CW, NT, E, LDS, DIR, EXACT, PASS + 1, NS * R, REV>(v, buf, tw);
   }
 }
 

@@ -155,17 +155,8 @@ struct ColCfg {
   static constexpr size_t TILE_BYTES = sizeof(C) * (size_t)N * LDS;
   __host__ __device__ static constexpr size_t tile_bytes() { return TILE_BYTES; }
   __host__ __device__ static constexpr size_t chat_bytes() { return sizeof(Real) * (size_t)(N / 2 + 1) * NCOL; }
-  // copy of the twiddle table (pairs, 2 N entries), after the tile and C^ values
-  static constexpr size_t TW_BYTES = sizeof(C) * (size_t)(2 * N);
-  __host__ __device__ static constexpr int fit(size_t b) { return (int)((228u * 1024u) / (b + 1024u)); }
   __host__ __device__ static constexpr size_t base_bytes(int var) { return tile_bytes() + (var == 5 ? chat_bytes() : 0); }
-  // the kernel-transform variant reads its table from shared memory when that
-  // costs no resident tile (measured faster there, slower in the other variants)
-  __host__ __device__ static constexpr bool tws(int var) {
-    return var == 5 &&
-           fit(base_bytes(var) + TW_BYTES) >= (fit(base_bytes(var)) < MINB ? fit(base_bytes(var)) : MINB);
-  }
-  __host__ __device__ static constexpr size_t smem_bytes(int var) { return base_bytes(var) + (tws(var) ? TW_BYTES : 0); }
+  __host__ __device__ static constexpr size_t smem_bytes(int var) { return base_bytes(var); }
 };
 
 template <typename Real, int N, int VAR>
@@ -239,18 +230,6 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
           (a.line_stride % 2 == 0);
   C v[E];
   Real* sC = reinterpret_cast<Real*>(smem_raw + K::TILE_BYTES);
-  constexpr bool TWS = K::tws(VAR);
-  if constexpr (TWS) {
-    // twiddle table to shared memory (its own cp.async group, waited for
-    // before the first exchange)
-    static_assert(K::base_bytes(VAR) % 16 == 0, "16-byte aligned table copy");
-    C* tws = reinterpret_cast<C*>(smem_raw + K::base_bytes(VAR));
-    constexpr int Q = (int)(2 * N * sizeof(C) / 16);
-    for (int q = tid; q < Q; q += NT)
-      cp_async<16>(reinterpret_cast<char*>(tws) + 16 * q, reinterpret_cast<const char*>(tw) + 16 * q);
-    cp_async_commit();
-    tw = tws;
-  }
   if constexpr (VAR == COL_KHAT) {
     // start fetching C^ (|p_row| = 0..N/2, this tile's columns) while the forward transform runs
     const Real* ch = reinterpret_cast<const Real*>(m.chat);
@@ -304,17 +283,10 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
       }
     }
   }
-  if constexpr (TWS) {
-    // the twiddle group has landed (the C^ group may still be in flight); the
-    // first exchange's barrier publishes the table to the block
-    if constexpr (VAR == COL_KHAT) cp_async_wait_group<1>();
-    else cp_async_wait_group<0>();
-    if constexpr (radix_plan(N).npass < 2) __syncthreads();
-  }
   if constexpr (VAR == COL_FWD || VAR == COL_INV || VAR == COL_PADF || VAR == COL_CROPI) {
-    regs_fft<C, N, NCP, CW, NT, E, LDS, DIR1, EXACT, 0, 1, false, TWS>(v, buf, tw);
+    regs_fft<C, N, NCP, CW, NT, E, LDS, DIR1, EXACT, 0, 1>(v, buf, tw);
   } else {
-    regs_fft<C, N, NCP, CW, NT, E, LDS, -1, EXACT, 0, 1, false, TWS>(v, buf, tw);
+    regs_fft<C, N, NCP, CW, NT, E, LDS, -1, EXACT, 0, 1>(v, buf, tw);
     // spectral multiplier on the outputs (row = frequency index along the axis)
     if constexpr (VAR == COL_KIN) {
       // kinetic phase exp(-i f theta_k) from the plan's octant table, indexed by
@@ -392,7 +364,7 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
       smem_to_regs<C, N, NCP, CW, NT, E, R0, LDS>(v, buf);
       __syncthreads();
     }
-    regs_fft<C, N, NCP, CW, NT, E, LDS, +1, EXACT, 0, 1, FUSED, TWS>(v, buf, tw);
+    regs_fft<C, N, NCP, CW, NT, E, LDS, +1, EXACT, 0, 1, FUSED>(v, buf, tw);
   }
   // outputs of the last pass to global memory (rows >= n_store cropped)
 #pragma unroll
