@@ -277,7 +277,7 @@ def main():
     ap.add_argument("--oracle-steps", type=int, default=1)
     ap.add_argument("--batched-steps", type=int, default=20)
     ap.add_argument("--gs-steps", type=int, default=20)
-    ap.add_argument("--configs", type=int, default=1, help="1: also time the other configurations")
+    ap.add_argument("--others", type=int, default=1, help="1: also time the other workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
@@ -421,9 +421,9 @@ def main():
 
     # the other configurations: steps/s of the 2D Coulomb (float64) and 128^3
     # dipolar (float32) runs, and forward + adjoint steps/s of the gradient run
-    configs = None
-    if args.configs:
-        configs = {}
+    others = None
+    if args.others:
+        others = {}
         for name in ("2d_coulomb_128", "3d_dipolar_128"):
             dc = I.workload(name)
             pc = fse.Plan(dc, stream=stream, device=dev)
@@ -434,7 +434,7 @@ def main():
             pc.step(xc, 5 * dc["dt"], dc["steps"])
             e1.record(stream)
             torch.cuda.synchronize(dev)
-            configs[name] = {"split_steps_per_s": dc["steps"] / (e0.elapsed_time(e1) / 1000.0),
+            others[name] = {"split_steps_per_s": dc["steps"] / (e0.elapsed_time(e1) / 1000.0),
                              "steps": dc["steps"], "dtype": dc["prec"]}
             del pc, xc
         from paper_1512_03210_gb300 import autograd as AG
@@ -456,7 +456,7 @@ def main():
         fwd_bwd()
         torch.cuda.synchronize(dev)
         sa = time.perf_counter() - t0a
-        configs["adjoint_2d_256"] = {"gradient_steps_per_s": da["steps"] / sa, "steps": da["steps"],
+        others["adjoint_2d_256"] = {"gradient_steps_per_s": da["steps"] / sa, "steps": da["steps"],
                                      "dtype": da["prec"],
                                      "note": "forward with sqrt(T) checkpoints, recomputation and adjoint; host-timed"}
         del pa
@@ -503,7 +503,7 @@ def main():
         "grid_point_steps_per_s": value * 256 ** 3,
         "model_bytes_per_step": step_bytes,
         "step_roofline_frac": step_bytes * value / world / 1e9 / peak,
-        "roofline": roofline, "kernels": kernels, "f64": f64, "e2e": e2e, "batched_2d": batched, "ground_state": gs, "configs": configs,
+        "roofline": roofline, "kernels": kernels, "f64": f64, "e2e": e2e, "batched_2d": batched, "ground_state": gs, "other_workloads": others,
         "cpu_baseline": cb, "gpu_launches": launches, "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
