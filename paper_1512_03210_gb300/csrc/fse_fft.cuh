@@ -262,7 +262,10 @@ __device__ __forceinline__ double2 unit_mul(double2 v, double c, double s, bool 
 }
 
 // One Stockham pass of radix R over NCOL lines of length N in shared memory.
-template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, int R, int NS>
+// ZIN (first pass): rows >= N/2 of the input are zero and are not read.
+// ZOUT (last pass): rows >= N/2 of the output are not needed and not stored.
+template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, int R, int NS, bool ZIN = false,
+          bool ZOUT = false>
 __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) {
   constexpr int LDS = NCOL + 1;
   constexpr int ITEMS = NCOL * (N / R);
@@ -275,7 +278,9 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
     if ((ITEMS % NT) == 0 || w < ITEMS) {
       const int c = w % NCOL, j = w / NCOL;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[it][r] = buf[(j + r * (N / R)) * LDS + c];
+      for (int r = 0; r < R; ++r)
+        v[it][r] = (ZIN && 2 * r >= R) ? mk(decltype(v[0][0].x)(0), decltype(v[0][0].x)(0))
+                                        : buf[(j + r * (N / R)) * LDS + c];
       if constexpr (NS > 1) {
         const int k = j % NS;
 #pragma unroll
@@ -293,28 +298,32 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
       const int k = j % NS;
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[(base + r * NS) * LDS + c] = v[it][r];
+      for (int r = 0; r < R; ++r)
+        if (!(ZOUT && 2 * r >= R)) buf[(base + r * NS) * LDS + c] = v[it][r];
     }
   }
   __syncthreads();
 }
 
-template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, int PASS, int NS>
+template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, int PASS, int NS, bool ZIN, bool ZOUT>
 __device__ __forceinline__ void stockham_rec(C* buf, const C* __restrict__ tw) {
   constexpr RadixPlan P = radix_plan(N);
   if constexpr (PASS < P.npass) {
     constexpr int R = P.r[PASS];
-    stockham_pass<C, N, NCOL, NT, DIR, EXACT, R, NS>(buf, tw);
-    stockham_rec<C, N, NCOL, NT, DIR, EXACT, PASS + 1, NS * R>(buf, tw);
+    stockham_pass<C, N, NCOL, NT, DIR, EXACT, R, NS, ZIN && PASS == 0, ZOUT && PASS + 1 == P.npass>(buf, tw);
+    stockham_rec<C, N, NCOL, NT, DIR, EXACT, PASS + 1, NS * R, ZIN, ZOUT>(buf, tw);
   }
 }
 
 // Full transform of NCOL lines of length N held in buf (caller synchronised
-// before the call; the call ends with a barrier).
-template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT>
+// before the call; the call ends with a barrier). ZIN: the input's rows >= N/2
+// are zero (inputs r of the first pass with 2 r >= R lie there for every j and
+// are not read); ZOUT: only output rows < N/2 are needed (outputs r of the last
+// pass with 2 r >= R are not stored).
+template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, bool ZIN = false, bool ZOUT = false>
 __device__ __forceinline__ void fft_tile(C* buf, const C* __restrict__ tw) {
   static_assert(fft_size_ok(N), "FFT length must be 2^a or 3*2^a");
-  stockham_rec<C, N, NCOL, NT, DIR, EXACT, 0, 1>(buf, tw);
+  stockham_rec<C, N, NCOL, NT, DIR, EXACT, 0, 1, ZIN, ZOUT>(buf, tw);
 }
 
 // ---------------------------------------------------------------------------

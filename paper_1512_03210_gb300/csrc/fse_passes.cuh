@@ -457,12 +457,17 @@ __device__ __forceinline__ void r2c_rows(const XArgs& a, typename Cplx<Real>::T*
       reinterpret_cast<Real*>(&buf[x * LDS2 + (l >> 1)])[l & 1] = val[it];
     }
   }
-  for (int idx = tid; idx < (NCOL / 2) * NX; idx += NT) {
-    const int q = idx / NX, x = NX + idx % NX;
-    buf[x * LDS2 + q] = mk(Real(0), Real(0));
+  // Rows NX..2NX-1 are the zero padding. With an even first radix the first
+  // pass reads none of them (it takes them as zero); with radix 3 it reads rows
+  // 2NX/3..4NX/3-1, part of which lie there, so those are zero-filled first.
+  if constexpr (radix_plan(2 * NX).r[0] % 2 != 0) {
+    for (int idx = tid; idx < (NCOL / 2) * NX; idx += NT) {
+      const int q = idx / NX, x = NX + idx % NX;
+      buf[x * LDS2 + q] = mk(Real(0), Real(0));
+    }
   }
   __syncthreads();
-  fft_tile<C, 2 * NX, NCOL / 2, NT, -1, false>(buf, tw2n);
+  fft_tile<C, 2 * NX, NCOL / 2, NT, -1, false, true, false>(buf, tw2n);
   const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
   constexpr int NH = (NCOL / 2) * (NX + 1), PH = (NH + NT - 1) / NT;
 #pragma unroll
@@ -510,7 +515,8 @@ __device__ __forceinline__ void c2r_rows(const XArgs& a, typename Cplx<Real>::T*
     }
   }
   __syncthreads();
-  fft_tile<C, 2 * NX, NCOL / 2, NT, +1, false>(buf, tw2n);
+  // only rows 0..NX-1 survive the crop: the last pass stores no others
+  fft_tile<C, 2 * NX, NCOL / 2, NT, +1, false, false, true>(buf, tw2n);
 #pragma unroll
   for (int it = 0; it < PER; ++it) {
     const int idx = tid + it * NT;
