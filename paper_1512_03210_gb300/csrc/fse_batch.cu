@@ -45,6 +45,7 @@ k_colpass_batch(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__
     m.conj = conj;
   } else {
     m.a0 = r.dt * m.scale;
+    m.f.a0 = (float)m.a0;
   }
   colpass_body<Real, N, VAR>(a, m, tw, blockIdx.x);
 }
@@ -67,6 +68,7 @@ k_xpass_batch(XArgs a, const typename Cplx<Real>::T* __restrict__ twn, const typ
     a.pe = 0.0;
     a.beta_dt = r.beta * r.dt;
     a.lam = r.lam;
+    fill_f32_phase(a);
   }
   xpass_body<Real, NX, KIND>(a, twn, tw2n, blockIdx.x);
 }
@@ -80,7 +82,9 @@ static cudaError_t colb(const ColArgs& a, const MulArgs& m, const void* tw, cons
   cudaError_t e = allow_smem(k_colpass_batch<float, N, VAR>, smem, done);
   if (e != cudaSuccess) return e;
   dim3 grid(a.nplanes * a.tiles_per_plane, nr);
-  k_colpass_batch<float, N, VAR><<<grid, K::NT, smem, st>>>(a, m, reinterpret_cast<const float2*>(tw), runs, on_spec,
+  MulArgs mf = m;
+  fill_f32(mf);
+  k_colpass_batch<float, N, VAR><<<grid, K::NT, smem, st>>>(a, mf, reinterpret_cast<const float2*>(tw), runs, on_spec,
                                                              kin_full, conj);
   return cudaGetLastError();
 }
@@ -108,7 +112,9 @@ static cudaError_t xb(const XArgs& a, const void* twn, const void* tw2n, const B
   cudaError_t e = allow_smem(k_xpass_batch<float, NX, KIND>, smem, done);
   if (e != cudaSuccess) return e;
   dim3 grid((a.nlines + K::NCOL - 1) / K::NCOL, nr);
-  k_xpass_batch<float, NX, KIND><<<grid, K::NT, smem, st>>>(a, reinterpret_cast<const float2*>(twn),
+  XArgs af = a;
+  fill_f32(af);
+  k_xpass_batch<float, NX, KIND><<<grid, K::NT, smem, st>>>(af, reinterpret_cast<const float2*>(twn),
                                                             reinterpret_cast<const float2*>(tw2n), runs, t0, step);
   return cudaGetLastError();
 }

@@ -37,7 +37,9 @@ static cudaError_t col_launch(const ColArgs& a, const MulArgs& m, const void* tw
   const long long blocks = col_blocks(a, K::NCOL);
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-  k_colpass<Real, N, VAR><<<(unsigned)blocks, K::NT, smem, st>>>(a, m, reinterpret_cast<const C*>(tw));
+  MulArgs mf = m;
+  fill_f32(mf);
+  k_colpass<Real, N, VAR><<<(unsigned)blocks, K::NT, smem, st>>>(a, mf, reinterpret_cast<const C*>(tw));
   return cudaGetLastError();
 }
 
@@ -75,7 +77,9 @@ static cudaError_t x_launch(const XArgs& a, const void* twn, const void* tw2n, c
   if (e != cudaSuccess) return e;
   const int blocks = (a.nlines + K::NCOL - 1) / K::NCOL;
   if (blocks <= 0) return cudaSuccess;
-  k_xpass<Real, NX, KIND><<<blocks, K::NT, smem, st>>>(a, reinterpret_cast<const C*>(twn),
+  XArgs af = a;
+  fill_f32(af);
+  k_xpass<Real, NX, KIND><<<blocks, K::NT, smem, st>>>(af, reinterpret_cast<const C*>(twn),
                                                        reinterpret_cast<const C*>(tw2n));
   return cudaGetLastError();
 }

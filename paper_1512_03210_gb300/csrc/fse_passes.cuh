@@ -77,6 +77,13 @@ struct MulArgs {
   const void* kin;   // kinetic: octant table of exp(-i f theta_k) on |p_j| = 0..n_j/2
   long long kin_sp, kin_sr;  // kinetic: octant strides of the plane and row axes
   int conj;          // kinetic: multiply by the conjugate of the table (adjoint)
+  // float copies of the scalars above, written by fill_f32 before a launch: a
+  // float kernel reads them as they are instead of converting the double
+  // fields in every thread (double-to-float conversions issue on the narrow
+  // FP64 pipe)
+  struct {
+    float dkx, dkp, dkr, scale, a0, q[6];
+  } f;
 };
 
 struct XArgs {
@@ -101,7 +108,54 @@ struct XArgs {
   int lat_nq;
   double lat_w[16], lat_c[16], lat_s[16];
   void* out;              // pass R: optional real array receiving varphi (the nonlocal potential)
+  // float copies of the scalars above (see MulArgs::f)
+  struct {
+    float beta_dt, lam, pa, pb, pc, pe, lo0, lo1, lo2, h0, h1, h2;
+    float lat_amp, lat_k[3], lat_w[16], lat_c[16], lat_s[16];
+  } f;
 };
+
+__host__ __device__ inline void fill_f32(MulArgs& m) {
+  m.f.dkx = (float)m.dkx;
+  m.f.dkp = (float)m.dkp;
+  m.f.dkr = (float)m.dkr;
+  m.f.scale = (float)m.scale;
+  m.f.a0 = (float)m.a0;
+  for (int i = 0; i < 6; ++i) m.f.q[i] = (float)m.q[i];
+}
+
+// the step-dependent scalars of an x pass (phase coefficients)
+__host__ __device__ inline void fill_f32_phase(XArgs& a) {
+  a.f.beta_dt = (float)a.beta_dt;
+  a.f.lam = (float)a.lam;
+  a.f.pa = (float)a.pa;
+  a.f.pb = (float)a.pb;
+  a.f.pc = (float)a.pc;
+  a.f.pe = (float)a.pe;
+}
+
+__host__ __device__ inline void fill_f32(XArgs& a) {
+  fill_f32_phase(a);
+  a.f.lo0 = (float)a.lo0;
+  a.f.lo1 = (float)a.lo1;
+  a.f.lo2 = (float)a.lo2;
+  a.f.h0 = (float)a.h0;
+  a.f.h1 = (float)a.h1;
+  a.f.h2 = (float)a.h2;
+  a.f.lat_amp = (float)a.lat_amp;
+  for (int i = 0; i < 3; ++i) a.f.lat_k[i] = (float)a.lat_k[i];
+  for (int i = 0; i < 16; ++i) {
+    a.f.lat_w[i] = (float)a.lat_w[i];
+    a.f.lat_c[i] = (float)a.lat_c[i];
+    a.f.lat_s[i] = (float)a.lat_s[i];
+  }
+}
+
+// A scalar parameter in the kernel's precision: the double field, or its float copy.
+template <typename Real>
+__device__ __forceinline__ Real prm(double d, float f);
+template <> __device__ __forceinline__ float prm<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ double prm<double>(double d, float) { return d; }
 
 // Deterministic float64 block sum (blockDim.x a multiple of 32, <= 1024); result in lane 0 of warp 0.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -298,7 +352,7 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
         tab[q] = reinterpret_cast<const C*>(m.kin) + (m.lp ? (long long)abs(wrap_index(my_plane[q], m.lp)) * m.kin_sp : 0);
         ax[q] = abs(wrap_index(min(my_px[q], m.lx - 1), m.lx));
       }
-      const Real sc = Real(m.scale);
+      const Real sc = prm<Real>(m.scale, m.f.scale);
 #pragma unroll
       for (int i = 0; i < E / (RL * CW); ++i) {
         const int j = (tid + i * NT) / NCP;
@@ -324,13 +378,14 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
       Real Aq[CW], Bq[CW];
 #pragma unroll
       for (int q = 0; q < CW; ++q) {
-        const Real kp = m.lp ? Real(m.dkp) * Real(wrap_index(my_plane[q], m.lp)) : Real(0);
+        const Real kp = m.lp ? prm<Real>(m.dkp, m.f.dkp) * Real(wrap_index(my_plane[q], m.lp)) : Real(0);
         const Real kpo = (m.lp && 2 * my_plane[q] == m.lp) ? Real(0) : kp;
-        const Real kx = Real(m.dkx) * Real(my_px[q]);
+        const Real kx = prm<Real>(m.dkx, m.f.dkx) * Real(my_px[q]);
         const Real kxo = (2 * my_px[q] == m.lx) ? Real(0) : kx;
         // q(k) = A + B kr + q2 kr^2 (kr replaced by 0 in B at the Nyquist row)
-        Aq[q] = Real(m.q[0]) * kx * kx + Real(m.q[1]) * kp * kp + Real(m.q[3]) * kxo * kpo;
-        Bq[q] = Real(m.q[4]) * kxo + Real(m.q[5]) * kpo;
+        Aq[q] = prm<Real>(m.q[0], m.f.q[0]) * kx * kx + prm<Real>(m.q[1], m.f.q[1]) * kp * kp +
+                prm<Real>(m.q[3], m.f.q[3]) * kxo * kpo;
+        Bq[q] = prm<Real>(m.q[4], m.f.q[4]) * kxo + prm<Real>(m.q[5], m.f.q[5]) * kpo;
       }
 #pragma unroll
       for (int i = 0; i < E / (RL * CW); ++i) {
@@ -339,17 +394,17 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
         for (int r = 0; r < RL; ++r) {
           const int row = j + r * (N / RL);
           const int pr = wrap_index(row, m.lr);
-          const Real kr = Real(m.dkr) * Real(pr);
+          const Real kr = prm<Real>(m.dkr, m.f.dkr) * Real(pr);
           const Real kro = (2 * row == m.lr) ? Real(0) : kr;
 #pragma unroll
           for (int q = 0; q < CW; ++q) {
             const Real cv = sC[abs(pr) * NCOL + cg * CW + q];
             Real f;
             if (ddi) {
-              const Real qf = Aq[q] + Bq[q] * kro + Real(m.q[2]) * kr * kr;
-              f = Real(m.a0) + qf * cv;
+              const Real qf = Aq[q] + Bq[q] * kro + prm<Real>(m.q[2], m.f.q[2]) * kr * kr;
+              f = prm<Real>(m.a0, m.f.a0) + qf * cv;
             } else {
-              f = Real(m.a0) * cv;
+              f = prm<Real>(m.a0, m.f.a0) * cv;
             }
             const C x = v[(i * CW + q) * RL + r];
             if constexpr (FUSED) v[(i * CW + q) * RL + r] = mk(f * x.x, f * x.y);
@@ -559,28 +614,29 @@ template <> __device__ __forceinline__ double sin_sq(double v) {
 // frame (Gauss-Legendre nodes of the window in a.lat_*).
 template <typename Real>
 __device__ __noinline__ Real lattice_integral(const XArgs& a, Real X, Real Y, Real Z) {
-  const Real kx = Real(a.lat_k[0]), ky = Real(a.lat_k[1]);
-  const Real zt = a.lat_k[2] != 0.0 ? sin_sq(Real(a.lat_k[2]) * Z) : Real(0);
+  const Real kx = prm<Real>(a.lat_k[0], a.f.lat_k[0]), ky = prm<Real>(a.lat_k[1], a.f.lat_k[1]);
+  const Real kz = prm<Real>(a.lat_k[2], a.f.lat_k[2]);
+  const Real zt = kz != Real(0) ? sin_sq(kz * Z) : Real(0);
   Real acc = Real(0);
   for (int q = 0; q < a.lat_nq; ++q) {
-    const Real c = Real(a.lat_c[q]), s = Real(a.lat_s[q]);
+    const Real c = prm<Real>(a.lat_c[q], a.f.lat_c[q]), s = prm<Real>(a.lat_s[q], a.f.lat_s[q]);
     const Real xr = c * X + s * Y, yr = -s * X + c * Y;
-    acc += Real(a.lat_w[q]) * (sin_sq(kx * xr) + sin_sq(ky * yr) + zt);
+    acc += prm<Real>(a.lat_w[q], a.f.lat_w[q]) * (sin_sq(kx * xr) + sin_sq(ky * yr) + zt);
   }
-  return Real(a.lat_amp) * acc;
+  return prm<Real>(a.lat_amp, a.f.lat_amp) * acc;
 }
 
 // P at grid point (x, y, z): the harmonic quadratic form plus, with LAT = 1,
 // the optical lattice (LAT = 2: when lat_amp != 0, decided at run time)
 template <typename Real, int LAT>
 __device__ __forceinline__ Real trap_phase(const XArgs& a, int x, int y, int z) {
-  const Real X = Real(a.lo0) + Real(a.h0) * Real(x);
-  const Real Y = Real(a.lo1) + Real(a.h1) * Real(y);
-  const Real Z = Real(a.lo2) + Real(a.h2) * Real(z);
-  if (LAT == 1 || (LAT == 2 && a.lat_amp != 0.0))
-    return Real(a.pa) * X * X + Real(a.pb) * Y * Y + Real(a.pc) * X * Y + Real(a.pe) * Z * Z +
-           lattice_integral<Real>(a, X, Y, Z);
-  return Real(a.pa) * X * X + Real(a.pb) * Y * Y + Real(a.pc) * X * Y + Real(a.pe) * Z * Z;
+  const Real X = prm<Real>(a.lo0, a.f.lo0) + prm<Real>(a.h0, a.f.h0) * Real(x);
+  const Real Y = prm<Real>(a.lo1, a.f.lo1) + prm<Real>(a.h1, a.f.h1) * Real(y);
+  const Real Z = prm<Real>(a.lo2, a.f.lo2) + prm<Real>(a.h2, a.f.h2) * Real(z);
+  const Real P = prm<Real>(a.pa, a.f.pa) * X * X + prm<Real>(a.pb, a.f.pb) * Y * Y +
+                 prm<Real>(a.pc, a.f.pc) * X * Y + prm<Real>(a.pe, a.f.pe) * Z * Z;
+  if (LAT == 1 || (LAT == 2 && prm<Real>(a.lat_amp, a.f.lat_amp) != Real(0))) return P + lattice_integral<Real>(a, X, Y, Z);
+  return P;
 }
 
 template <typename Real, int NX, int KIND>
@@ -661,7 +717,8 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
           const long long o = (long long)lg * NX + x;
           const C u = u1p[o];
           const C g = psi[o];
-          const Real th = Real(a.beta_dt) * (u.x * u.x + u.y * u.y) + Real(a.lam) * vphi[it] + trap_phase<Real, 2>(a, x, yl, zl);
+          const Real th = prm<Real>(a.beta_dt, a.f.beta_dt) * (u.x * u.x + u.y * u.y) + prm<Real>(a.lam, a.f.lam) * vphi[it] +
+                           trap_phase<Real, 2>(a, x, yl, zl);
           Real sn, cs;
           sincos(th, &sn, &cs);
           const C u2 = mk(u.x * cs + u.y * sn, u.y * cs - u.x * sn);
@@ -705,7 +762,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
           const C u = u1p[o];
           const C h = psi[o];
           const Real r = h.x * u.y - h.y * u.x;
-          const Real q2 = Real(2) * (Real(a.beta_dt) * r + Real(a.lam) * kr[it]);
+          const Real q2 = Real(2) * (prm<Real>(a.beta_dt, a.f.beta_dt) * r + prm<Real>(a.lam, a.f.lam) * kr[it]);
           psi[o] = mk(h.x + q2 * u.x, h.y + q2 * u.y);
         }
       }
@@ -765,7 +822,8 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
             line_yz(y0, z0, l, a.ny, yl, zl);
             const C u = psi[(long long)lg * NX + x];
             const Real rho = u.x * u.x + u.y * u.y;
-            const Real th = Real(a.beta_dt) * rho + Real(a.lam) * vphi[it] + trap_phase<Real, KIND == XP_AL ? 1 : 0>(a, x, yl, zl);
+            const Real th = prm<Real>(a.beta_dt, a.f.beta_dt) * rho + prm<Real>(a.lam, a.f.lam) * vphi[it] +
+                             trap_phase<Real, KIND == XP_AL ? 1 : 0>(a, x, yl, zl);
             Real sn, cs;
             phase_sincos(th, &sn, &cs);
             u2 = unit_mul(u, cs, -sn, false);
