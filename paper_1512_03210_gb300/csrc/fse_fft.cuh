@@ -108,15 +108,31 @@ __host__ __device__ constexpr bool fft_size_ok(int N) {
 // ---------------------------------------------------------------------------
 // In-register DFTs of size R. DIR = -1 forward, +1 inverse.
 // ---------------------------------------------------------------------------
-template <int DIR, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
-  C t = a;
-  a = cadd(t, b);
-  b = csub(t, b);
+// ZH (dft2, dft4, dft8, and dft3 below): the inputs of the second half are
+// zero and are not read.
+template <int DIR, bool ZH = false, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+  if constexpr (ZH) {
+    b = a;
+  } else {
+    C t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+  }
 }
 
-template <int DIR, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
-  C s02 = cadd(a0, a2), d02 = csub(a0, a2);
-  C s13 = cadd(a1, a3), d13 = mul_i<DIR>(csub(a1, a3));
+template <int DIR, bool ZH = false, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  C s02, d02, s13, d13;
+  if constexpr (ZH) {
+    s02 = a0;
+    d02 = a0;
+    s13 = a1;
+    d13 = mul_i<DIR>(a1);
+  } else {
+    s02 = cadd(a0, a2);
+    d02 = csub(a0, a2);
+    s13 = cadd(a1, a3);
+    d13 = mul_i<DIR>(csub(a1, a3));
+  }
   a0 = cadd(s02, s13);
   a2 = csub(s02, s13);
   a1 = cadd(d02, d13);
@@ -150,11 +166,21 @@ template <bool EXACT, typename R> __device__ __forceinline__ R kmul(R x, R k1, R
   else return x * k1;
 }
 
-template <int DIR, bool EXACT, typename C> __device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
+// ZH: a2 is zero and not read (half of a zero-padded line). The zero inputs of
+// the ZH forms are left out rather than added: x + 0 is not folded by the
+// compiler (it would change the sign of a zero), so the sums would be issued.
+template <int DIR, bool EXACT, bool ZH = false, typename C>
+__device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
   typedef decltype(a0.x) R;
   const R c = R(-0.5);
-  C t = cadd(a1, a2);
-  C d = csub(a1, a2);
+  C t, d;
+  if constexpr (ZH) {
+    t = a1;
+    d = a1;
+  } else {
+    t = cadd(a1, a2);
+    d = csub(a1, a2);
+  }
   C m = mk(a0.x + c * t.x, a0.y + c * t.y);
   // i * DIR * sin(2 pi/3) * (a1 - a2): exp(DIR 2 pi i/3) = c + i DIR sin(2 pi/3)
   const R sy = kmul<EXACT>(d.y, Kc<R>::s1, Kc<R>::s2), sx = kmul<EXACT>(d.x, Kc<R>::s1, Kc<R>::s2);
@@ -164,11 +190,11 @@ template <int DIR, bool EXACT, typename C> __device__ __forceinline__ void dft3(
   a2 = csub(m, e);
 }
 
-template <int DIR, bool EXACT, typename C> __device__ __forceinline__ void dft8(C* v) {
+template <int DIR, bool EXACT, bool ZH = false, typename C> __device__ __forceinline__ void dft8(C* v) {
   typedef decltype(v[0].x) R;
-  // even / odd halves
-  dft4<DIR>(v[0], v[2], v[4], v[6]);
-  dft4<DIR>(v[1], v[3], v[5], v[7]);
+  // even / odd halves (with ZH, v[4..7] = 0 is the second half of each)
+  dft4<DIR, ZH>(v[0], v[2], v[4], v[6]);
+  dft4<DIR, ZH>(v[1], v[3], v[5], v[7]);
   // twiddle odd half by w8^k, w8 = exp(DIR i pi/4):
   // w8^1 = h (1 + DIR i); w8^2 = DIR i; w8^3 = h (-1 + DIR i), h = sqrt(1/2)
   C o1 = v[3], o2 = v[5], o3 = v[7];
@@ -190,16 +216,17 @@ template <int DIR, bool EXACT, typename C> __device__ __forceinline__ void dft8(
 
 // EXACT = false drops the tails of the irrational constants (transforms of the
 // density and potential, where a fixed 1e-8 scale error is harmless).
-template <int R, int DIR, bool EXACT = true, typename C> __device__ __forceinline__ void dft(C* v) {
+// ZH: inputs r with 2 r >= R are zero and are not read.
+template <int R, int DIR, bool EXACT = true, bool ZH = false, typename C> __device__ __forceinline__ void dft(C* v) {
   if constexpr (R == 2) {
-    dft2<DIR>(v[0], v[1]);
+    dft2<DIR, ZH>(v[0], v[1]);
   } else if constexpr (R == 3) {
-    dft3<DIR, EXACT>(v[0], v[1], v[2]);
+    dft3<DIR, EXACT, ZH>(v[0], v[1], v[2]);
   } else if constexpr (R == 4) {
-    dft4<DIR>(v[0], v[1], v[2], v[3]);
+    dft4<DIR, ZH>(v[0], v[1], v[2], v[3]);
   } else {
     static_assert(R == 8, "radix");
-    dft8<DIR, EXACT>(v);
+    dft8<DIR, EXACT, ZH>(v);
   }
 }
 
@@ -286,7 +313,7 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
 #pragma unroll
         for (int r = 1; r < R; ++r) v[it][r] = twiddle_mul<DIR, EXACT>(v[it][r], tw, (k * r) * (N / (NS * R)));
       }
-      dft<R, DIR, EXACT>(v[it]);
+      dft<R, DIR, EXACT, ZIN>(v[it]);
     }
   }
   __syncthreads();
@@ -365,8 +392,10 @@ __device__ __forceinline__ void ld_pair(const float2* p, float2& a, float2& b) {
   b = make_float2(t.z, t.w);
 }
 
-template <typename C, int N, int NCP, int CW, int NT, int E, int DIR, bool EXACT, int R, int NS>
+// ZIN (a first pass, NS = 1): inputs r with 2 r >= R are zero and are not read.
+template <typename C, int N, int NCP, int CW, int NT, int E, int DIR, bool EXACT, int R, int NS, bool ZIN = false>
 __device__ __forceinline__ void regs_pass(C (&v)[E], const C* __restrict__ tw) {
+  static_assert(!ZIN || NS == 1, "zero inputs only in a first pass");
   constexpr int I = E / (R * CW);
   const int tid = threadIdx.x;
 #pragma unroll
@@ -383,7 +412,7 @@ __device__ __forceinline__ void regs_pass(C (&v)[E], const C* __restrict__ tw) {
       }
     }
 #pragma unroll
-    for (int q = 0; q < CW; ++q) dft<R, DIR, EXACT>(&v[(i * CW + q) * R]);
+    for (int q = 0; q < CW; ++q) dft<R, DIR, EXACT, ZIN>(&v[(i * CW + q) * R]);
   }
 }
 
@@ -438,13 +467,14 @@ __host__ __device__ constexpr int plan_radix(int p) {
 // holds the outputs of the last pass at positions j + r N/R_last. With REV the
 // radices are taken in reverse order: a transform whose inputs are the outputs
 // of a forward-order transform (positions j + r N/R_last) then starts without an
-// exchange, since its first radix is that transform's last one.
+// exchange, since its first radix is that transform's last one. ZIN: the
+// inputs at rows >= N/2 are zero (a zero-padded line) and pass 0 does not read them.
 template <typename C, int N, int NCP, int CW, int NT, int E, int LDS, int DIR, bool EXACT, int PASS, int NS,
-          bool REV = false>
+          bool REV = false, bool ZIN = false>
 __device__ __forceinline__ void regs_fft(C (&v)[E], C* buf, const C* __restrict__ tw) {
   constexpr int NP = radix_plan(N).npass;
   constexpr int R = plan_radix<N, REV>(PASS);
-  regs_pass<C, N, NCP, CW, NT, E, DIR, EXACT, R, NS>(v, tw);
+  regs_pass<C, N, NCP, CW, NT, E, DIR, EXACT, R, NS, ZIN && PASS == 0>(v, tw);
   if constexpr (PASS + 1 < NP) {
     constexpr int R2 = plan_radix<N, REV>(PASS + 1);
     regs_to_smem<C, N, NCP, CW, NT, E, R, NS, LDS>(v, buf);

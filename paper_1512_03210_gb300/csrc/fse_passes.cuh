@@ -213,9 +213,13 @@ struct ColCfg {
   __host__ __device__ static constexpr size_t smem_bytes(int var) { return base_bytes(var); }
 };
 
-template <typename Real, int N, int VAR>
-__device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
-                                             const typename Cplx<Real>::T* __restrict__ tw, int bid) {
+// One tile of a column pass: NCOL adjacent columns of one plane, or (GATHER)
+// NCOL (plane, column) pairs of the tail columns. The two kinds are separate
+// instantiations, so that the per-column state of the gathered tiles does not
+// take registers from the full ones.
+template <typename Real, int N, int VAR, bool GATHER>
+__device__ __forceinline__ void colpass_tile(const ColArgs& a, const MulArgs& m,
+                                             const typename Cplx<Real>::T* __restrict__ tw, int bid, int ngat) {
   typedef ColCfg<Real, N> K;
   typedef typename K::C C;
   constexpr int NCOL = K::NCOL, NCP = K::NCP, CW = K::CW, LDS = K::LDS, NT = K::NT, E = K::E;
@@ -238,11 +242,7 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
   const int tid = threadIdx.x;
   static_assert(NT % NCP == 0, "a thread keeps one column group of the tile");
   const int cg = tid % NCP;  // this thread's columns of the tile: cg CW + q, q < CW
-  // only passes over R2C bins (ncols = nx + 1) have tail tiles; they come
-  // first in the grid, so that they overlap the full tiles
-  constexpr bool TAILS = (VAR == COL_PADF || VAR == COL_CROPI || VAR == COL_KHAT);
-  const int ngat = TAILS && a.tail > 0 ? (a.nplanes * a.tail + NCOL - 1) / NCOL : 0;
-  const bool gather = bid < ngat;
+  constexpr bool gather = GATHER;
   const int breg = bid - ngat;
   const int tp = gather ? 0 : breg / a.tiles_per_plane;
   const int c0 = gather ? 0 : (breg - tp * a.tiles_per_plane) * NCOL;
@@ -338,9 +338,9 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
     }
   }
   if constexpr (VAR == COL_FWD || VAR == COL_INV || VAR == COL_PADF || VAR == COL_CROPI) {
-    regs_fft<C, N, NCP, CW, NT, E, LDS, DIR1, EXACT, 0, 1>(v, buf, tw);
+    regs_fft<C, N, NCP, CW, NT, E, LDS, DIR1, EXACT, 0, 1, false, HALF_IN>(v, buf, tw);
   } else {
-    regs_fft<C, N, NCP, CW, NT, E, LDS, -1, EXACT, 0, 1>(v, buf, tw);
+    regs_fft<C, N, NCP, CW, NT, E, LDS, -1, EXACT, 0, 1, false, HALF_IN>(v, buf, tw);
     // spectral multiplier on the outputs (row = frequency index along the axis)
     if constexpr (VAR == COL_KIN) {
       // kinetic phase exp(-i f theta_k) from the plan's octant table, indexed by
@@ -442,6 +442,22 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
         if (my_ok[0]) colp[0][(long long)row * a.line_stride] = v[i * RF + r];
       }
     }
+  }
+}
+
+template <typename Real, int N, int VAR>
+__device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
+                                             const typename Cplx<Real>::T* __restrict__ tw, int bid) {
+  // only passes over R2C bins (ncols = nx + 1) have tail tiles; they come
+  // first in the grid, so that they overlap the full tiles
+  constexpr bool TAILS = (VAR == COL_PADF || VAR == COL_CROPI || VAR == COL_KHAT);
+  if constexpr (TAILS) {
+    constexpr int NCOL = ColCfg<Real, N>::NCOL;
+    const int ngat = a.tail > 0 ? (a.nplanes * a.tail + NCOL - 1) / NCOL : 0;
+    if (bid < ngat) colpass_tile<Real, N, VAR, true>(a, m, tw, bid, ngat);
+    else colpass_tile<Real, N, VAR, false>(a, m, tw, bid, ngat);
+  } else {
+    colpass_tile<Real, N, VAR, false>(a, m, tw, bid, 0);
   }
 }
 
