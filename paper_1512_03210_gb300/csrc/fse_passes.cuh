@@ -785,8 +785,11 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
     }
   } else {
     // XP_A / XP_R: varphi from the cropped C2R of S
-    if ((KIND == XP_A || KIND == XP_AL) && tid == 0 && l0 < a.nlines) {
-      // the tile's rows of psi (contiguous) move to L2 while the C2R runs
+    if ((KIND == XP_A || KIND == XP_AL) && tid == 0 && l0 < a.nlines &&
+        (reinterpret_cast<uintptr_t>(psi) & 15) == 0) {
+      // the tile's rows of psi (contiguous) move to L2 while the C2R runs (the
+      // bulk prefetch needs a 16-byte aligned start; psi may be only
+      // element-aligned, and every line then starts 16-byte aligned too)
       const int nl = min(NCOL, a.nlines - l0);
       prefetch_l2_bulk(psi + (long long)l0 * NX, (unsigned)(nl * NX * sizeof(C)));
     }

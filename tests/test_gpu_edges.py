@@ -48,6 +48,32 @@ def test_bad_arguments_are_rejected_before_any_launch(lib):
     assert plan.launches == n0
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_element_aligned_psi_matches_aligned_psi(lib, dim):
+    """A float32 field 8- but not 16-byte aligned (one element into its buffer)
+    takes the element-wise global accesses of the column passes instead of the
+    16-byte ones, and pass A leaves out its bulk L2 prefetch (which needs a
+    16-byte aligned start); its steps are bit-identical to those of the same
+    field 16-byte aligned."""
+    if dim == 2:
+        d = dict(dim=2, n=(64, 48), lo=(-6.0, -5.0), hi=(6.0, 5.0), s=0.7, omega=0.5, beta=20.0, lam=5.0,
+                 kernel="coulomb", gamma=(1.0, 1.2), dt=1e-2, prec="f32")
+    else:
+        d = dict(dim=3, n=(32, 24, 48), lo=(-5.0, -4.0, -6.0), hi=(5.0, 4.0, 6.0), s=0.7, omega=0.8, beta=50.0,
+                 lam=20.0, kernel="ddi3d", dip_n=(1 / math.sqrt(2), 0.0, 1 / math.sqrt(2)),
+                 gamma=(1.0, 1.2, 2.0), dt=5e-3, prec="f32")
+    plan = lib.Plan(d)
+    x = plan.to_device(_gauss(O.params(d)))
+    buf = torch.empty(x.numel() + 1, dtype=x.dtype, device=x.device)
+    y = buf[1:].view(x.shape)
+    y.copy_(x)
+    assert x.data_ptr() % 16 == 0 and y.data_ptr() % 16 == 8
+    plan.step(x, 0.0, 3)
+    plan.step(y, 0.0, 3)
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+
+
 @pytest.mark.parametrize("n", [(256, 8, 8), (8, 8, 8), (8, 256, 16), (24, 12, 96)])
 def test_extreme_axis_lengths_3d_f64(lib, n):
     """Long x lines against the shortest y and z tiles, the smallest grid, and

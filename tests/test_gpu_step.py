@@ -184,6 +184,22 @@ def test_2d_f32_matches_oracle(lib):
     assert _rel(got, ref) < 4 * 5e-6
 
 
+def test_2d_f32_large_phases_match_oracle(lib):
+    """Potential phases of up to ~20 rad (dt = 0.5): the float path's branch
+    for |Theta| > 1/2 (sincosf rather than the short series) against the
+    oracle. Rounding of Theta itself (ulp(20) = 2e-6) bounds the agreement at
+    a few 1e-6 per step."""
+    d = _case2d(n=(64, 48), prec="f32", dt=0.5)
+    p = O.params(d)
+    psi0 = _gauss(p)
+    X = O.coords(p)
+    trap = 0.5 * d["dt"] * sum(g * g * X[j] ** 2 for j, g in enumerate(d["gamma"]))
+    assert trap.max() > 10.0  # the step crosses the reduced branch
+    ref = O.evolve(psi0, p, 0.0, 1)
+    got, _ = _run_gpu(lib, d, psi0, 0.0, 1)
+    assert _rel(got, ref) < 2e-5
+
+
 def test_3d_ddi_f32_matches_oracle(lib):
     d = _case3d(n=(32, 24, 48), prec="f32")
     p = O.params(d)
