@@ -2,7 +2,8 @@
 //
 // The transform along one grid axis is done on a tile of NCOL independent
 // lines held in shared memory as buf[j * LDS + c] (j = position along the
-// line, c = line within the tile, LDS = NCOL + 1). Each radix-R pass of the
+// line, c = line within the tile, LDS = NCOL + 1; or a swizzled layout
+// without padding for tiles of 8 lines, see tile_at). Each radix-R pass of the
 // mixed-radix Stockham autosort algorithm (radices 8, 4, 3, 2) reads R
 // elements at stride N/R, applies the twiddles, does an in-register DFT of
 // size R and writes the R results at stride Ns; all reads of a pass happen
@@ -288,13 +289,29 @@ __device__ __forceinline__ double2 unit_mul(double2 v, double c, double s, bool 
   return make_double2(v.x * c - v.y * sc, v.x * sc + v.y * c);
 }
 
+// Element (row, c) of a shared-memory tile of NCOL lines. The plain layout
+// pads rows to NCOL + 1 elements. The swizzled one (SWZ, for NCOL = 8) keeps
+// rows of NCOL elements and stores column c at c ^ ((row >> 1) & 7): the four
+// consecutive rows that a warp's 32 items touch in a Stockham pass then cover
+// every bank twice, where the padded layout of 9 put up to three accesses on
+// one bank.
+template <int NCOL, bool SWZ>
+__host__ __device__ constexpr int tile_ld() {
+  return SWZ ? NCOL : NCOL + 1;
+}
+template <int NCOL, bool SWZ>
+__device__ __forceinline__ int tile_at(int row, int c) {
+  static_assert(!SWZ || NCOL == 8, "the swizzled layout is for tiles of 8 lines");
+  if constexpr (SWZ) return row * NCOL + (c ^ ((row >> 1) & 7));
+  else return row * (NCOL + 1) + c;
+}
+
 // One Stockham pass of radix R over NCOL lines of length N in shared memory.
 // ZIN (first pass): rows >= N/2 of the input are zero and are not read.
 // ZOUT (last pass): rows >= N/2 of the output are not needed and not stored.
 template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, int R, int NS, bool ZIN = false,
-          bool ZOUT = false>
+          bool ZOUT = false, bool SWZ = false>
 __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) {
-  constexpr int LDS = NCOL + 1;
   constexpr int ITEMS = NCOL * (N / R);
   constexpr int PER = (ITEMS + NT - 1) / NT;
   const int tid = threadIdx.x;
@@ -307,7 +324,7 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
 #pragma unroll
       for (int r = 0; r < R; ++r)
         v[it][r] = (ZIN && 2 * r >= R) ? mk(decltype(v[0][0].x)(0), decltype(v[0][0].x)(0))
-                                        : buf[(j + r * (N / R)) * LDS + c];
+                                        : buf[tile_at<NCOL, SWZ>(j + r * (N / R), c)];
       if constexpr (NS > 1) {
         const int k = j % NS;
 #pragma unroll
@@ -326,19 +343,19 @@ __device__ __forceinline__ void stockham_pass(C* buf, const C* __restrict__ tw) 
       const int base = (j / NS) * NS * R + k;
 #pragma unroll
       for (int r = 0; r < R; ++r)
-        if (!(ZOUT && 2 * r >= R)) buf[(base + r * NS) * LDS + c] = v[it][r];
+        if (!(ZOUT && 2 * r >= R)) buf[tile_at<NCOL, SWZ>(base + r * NS, c)] = v[it][r];
     }
   }
   __syncthreads();
 }
 
-template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, int PASS, int NS, bool ZIN, bool ZOUT>
+template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, int PASS, int NS, bool ZIN, bool ZOUT, bool SWZ>
 __device__ __forceinline__ void stockham_rec(C* buf, const C* __restrict__ tw) {
   constexpr RadixPlan P = radix_plan(N);
   if constexpr (PASS < P.npass) {
     constexpr int R = P.r[PASS];
-    stockham_pass<C, N, NCOL, NT, DIR, EXACT, R, NS, ZIN && PASS == 0, ZOUT && PASS + 1 == P.npass>(buf, tw);
-    stockham_rec<C, N, NCOL, NT, DIR, EXACT, PASS + 1, NS * R, ZIN, ZOUT>(buf, tw);
+    stockham_pass<C, N, NCOL, NT, DIR, EXACT, R, NS, ZIN && PASS == 0, ZOUT && PASS + 1 == P.npass, SWZ>(buf, tw);
+    stockham_rec<C, N, NCOL, NT, DIR, EXACT, PASS + 1, NS * R, ZIN, ZOUT, SWZ>(buf, tw);
   }
 }
 
@@ -346,11 +363,13 @@ __device__ __forceinline__ void stockham_rec(C* buf, const C* __restrict__ tw) {
 // before the call; the call ends with a barrier). ZIN: the input's rows >= N/2
 // are zero (inputs r of the first pass with 2 r >= R lie there for every j and
 // are not read); ZOUT: only output rows < N/2 are needed (outputs r of the last
-// pass with 2 r >= R are not stored).
-template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, bool ZIN = false, bool ZOUT = false>
+// pass with 2 r >= R are not stored). SWZ: the tile uses the swizzled layout
+// (tile_at).
+template <typename C, int N, int NCOL, int NT, int DIR, bool EXACT, bool ZIN = false, bool ZOUT = false,
+          bool SWZ = false>
 __device__ __forceinline__ void fft_tile(C* buf, const C* __restrict__ tw) {
   static_assert(fft_size_ok(N), "FFT length must be 2^a or 3*2^a");
-  stockham_rec<C, N, NCOL, NT, DIR, EXACT, 0, 1, ZIN, ZOUT>(buf, tw);
+  stockham_rec<C, N, NCOL, NT, DIR, EXACT, 0, 1, ZIN, ZOUT, SWZ>(buf, tw);
 }
 
 // ---------------------------------------------------------------------------

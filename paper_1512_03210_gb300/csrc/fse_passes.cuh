@@ -479,7 +479,11 @@ struct XCfg {
   static constexpr int NCOL = ncol_for(2 * NX, sizeof(C)) < 2 ? 2 : ncol_for(2 * NX, sizeof(C));
   static constexpr int NT = 256;
   static constexpr int LDS = NCOL + 1;
-  static constexpr int LDS2 = NCOL / 2 + 1;
+  // the R2C / C2R of two real lines per complex line works on NCOL / 2
+  // lines of length 2 NX; with 8 of them it uses the swizzled tile layout
+  static constexpr bool SWZ2 = (NCOL / 2 == 8);
+  static constexpr int LDS2 = tile_ld<NCOL / 2, SWZ2>();
+  __device__ __forceinline__ static int pk(int row, int q) { return tile_at<NCOL / 2, SWZ2>(row, q); }
   static constexpr int TOT = NCOL * NX;
   static constexpr int PER = (TOT + NT - 1) / NT;
   static constexpr int MINB = sizeof(Real) == 4 ? 4 : 2;
@@ -517,7 +521,7 @@ __device__ __forceinline__ void r2c_rows(const XArgs& a, typename Cplx<Real>::T*
                                          const Real (&val)[XCfg<Real, NX>::PER]) {
   typedef XCfg<Real, NX> K;
   typedef typename K::C C;
-  constexpr int NCOL = K::NCOL, NT = K::NT, LDS2 = K::LDS2, TOT = K::TOT, PER = K::PER;
+  constexpr int NCOL = K::NCOL, NT = K::NT, TOT = K::TOT, PER = K::PER;
   const int tid = threadIdx.x;
   C* S = reinterpret_cast<C*>(a.spec);
 #pragma unroll
@@ -525,7 +529,7 @@ __device__ __forceinline__ void r2c_rows(const XArgs& a, typename Cplx<Real>::T*
     const int idx = tid + it * NT;
     if ((TOT % NT) == 0 || idx < TOT) {
       const int l = idx / NX, x = idx % NX;
-      reinterpret_cast<Real*>(&buf[x * LDS2 + (l >> 1)])[l & 1] = val[it];
+      reinterpret_cast<Real*>(&buf[K::pk(x, l >> 1)])[l & 1] = val[it];
     }
   }
   // Rows NX..2NX-1 are the zero padding. With an even first radix the first
@@ -534,11 +538,11 @@ __device__ __forceinline__ void r2c_rows(const XArgs& a, typename Cplx<Real>::T*
   if constexpr (radix_plan(2 * NX).r[0] % 2 != 0) {
     for (int idx = tid; idx < (NCOL / 2) * NX; idx += NT) {
       const int q = idx / NX, x = NX + idx % NX;
-      buf[x * LDS2 + q] = mk(Real(0), Real(0));
+      buf[K::pk(x, q)] = mk(Real(0), Real(0));
     }
   }
   __syncthreads();
-  fft_tile<C, 2 * NX, NCOL / 2, NT, -1, false, true, false>(buf, tw2n);
+  fft_tile<C, 2 * NX, NCOL / 2, NT, -1, false, true, false, K::SWZ2>(buf, tw2n);
   const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
   constexpr int NH = (NCOL / 2) * (NX + 1), PH = (NH + NT - 1) / NT;
 #pragma unroll
@@ -546,8 +550,8 @@ __device__ __forceinline__ void r2c_rows(const XArgs& a, typename Cplx<Real>::T*
     const int idx = tid + it * NT;
     if (idx < NH) {
       const int q = idx / (NX + 1), k = idx % (NX + 1);
-      const C zk = buf[k * LDS2 + q];
-      const C zm = buf[((2 * NX - k) % (2 * NX)) * LDS2 + q];
+      const C zk = buf[K::pk(k, q)];
+      const C zm = buf[K::pk((2 * NX - k) % (2 * NX), q)];
       const int la = l0 + 2 * q;
       const C A = mk(Real(0.5) * (zk.x + zm.x), Real(0.5) * (zk.y - zm.y));
       const C B = mk(Real(0.5) * (zk.y + zm.y), Real(0.5) * (zm.x - zk.x));
@@ -567,7 +571,7 @@ __device__ __forceinline__ void c2r_rows(const XArgs& a, typename Cplx<Real>::T*
                                          Real (&val)[XCfg<Real, NX>::PER]) {
   typedef XCfg<Real, NX> K;
   typedef typename K::C C;
-  constexpr int NCOL = K::NCOL, NT = K::NT, LDS2 = K::LDS2, TOT = K::TOT, PER = K::PER;
+  constexpr int NCOL = K::NCOL, NT = K::NT, TOT = K::TOT, PER = K::PER;
   const int tid = threadIdx.x;
   const C* S = reinterpret_cast<const C*>(a.spec);
   const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
@@ -581,20 +585,20 @@ __device__ __forceinline__ void c2r_rows(const XArgs& a, typename Cplx<Real>::T*
       C A = mk(Real(0), Real(0)), B = A;
       if (la < a.nlines) A = S[srow(y0, z0, 2 * q, a.ny, a.srow_mul) * a.sx + k];
       if (la + 1 < a.nlines) B = S[srow(y0, z0, 2 * q + 1, a.ny, a.srow_mul) * a.sx + k];
-      buf[k * LDS2 + q] = mk(A.x - B.y, A.y + B.x);
-      if (k > 0 && k < NX) buf[(2 * NX - k) * LDS2 + q] = mk(A.x + B.y, B.x - A.y);
+      buf[K::pk(k, q)] = mk(A.x - B.y, A.y + B.x);
+      if (k > 0 && k < NX) buf[K::pk(2 * NX - k, q)] = mk(A.x + B.y, B.x - A.y);
     }
   }
   __syncthreads();
   // only rows 0..NX-1 survive the crop: the last pass stores no others
-  fft_tile<C, 2 * NX, NCOL / 2, NT, +1, false, false, true>(buf, tw2n);
+  fft_tile<C, 2 * NX, NCOL / 2, NT, +1, false, false, true, K::SWZ2>(buf, tw2n);
 #pragma unroll
   for (int it = 0; it < PER; ++it) {
     const int idx = tid + it * NT;
     val[it] = Real(0);
     if ((TOT % NT) == 0 || idx < TOT) {
       const int l = idx / NX, x = idx % NX;
-      const C z = buf[x * LDS2 + (l >> 1)];
+      const C z = buf[K::pk(x, l >> 1)];
       val[it] = (l & 1) ? z.y : z.x;
     }
   }
