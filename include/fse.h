@@ -215,13 +215,16 @@ fse_status fse_plan_profile_read(fse_plan_t plan, double* ms, long long* count);
  * together: runs of equal grid size share one launch per pass and one kernel
  * transform; a run advanced in a batch is bit-identical to the same run
  * advanced alone with fse_step. Requirements: dim 2, FSE_F32, renormalize 0, order 2, no lattice,
- * one box and one kernel (none or Coulomb) for the whole batch. */
+ * one box, one kernel (none or Coulomb), one exponent mu and one Gaussian-sum
+ * fit (gs_delta, gs_h, gs_tmin after defaults) for the whole batch. */
 typedef struct fse_batch* fse_batch_t;
 
-/* Validate runs[0..nruns), create the batch on cuda_stream and return the
- * device workspace size it needs. Errors: FSE_ERR_INVALID (null, nruns <= 0,
- * DDI kernel), FSE_ERR_UNSUPPORTED (a requirement above not met, or a run's
- * own fse_plan_create error). */
+/* Validate runs[0..nruns) (every run gets the parameter checks of
+ * fse_plan_create), create the batch on cuda_stream and return the device
+ * workspace size it needs. Errors: FSE_ERR_INVALID (null, nruns <= 0, DDI
+ * kernel, a run that fse_plan_create would reject as invalid),
+ * FSE_ERR_UNSUPPORTED (a requirement above not met, or an unsupported grid
+ * size). */
 fse_status fse_batch_create(const fse_params* runs, int nruns, void* cuda_stream, fse_batch_t* out,
                             size_t* workspace_bytes);
 /* Attach caller-owned device memory (256-byte aligned, at least the size

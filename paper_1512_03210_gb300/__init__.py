@@ -291,8 +291,25 @@ def fse_plan_profile_read(plan) -> dict:
 
 def fse_mass_noalloc(psi, prec: str, npoints: int, cell_volume: float, mass_out, stream=None):
     """Mass of psi into mass_out (a one-element float64 device tensor) with no device
-    allocation; for callers that cannot allocate (see include/fse.h)."""
-    st = load().fse_mass_noalloc(_ptr(psi), PRECS[prec], int(npoints), float(cell_volume), _ptr(mass_out),
+    allocation; for callers that cannot allocate (see include/fse.h).
+
+    The C entry point sees only a pointer and a count, so the tensors are
+    checked here: psi a contiguous CUDA tensor of the dtype that prec names
+    (complex64 for "f32", complex128 for "f64") holding at least npoints
+    values, mass_out a CUDA float64 tensor on the same device."""
+    import torch
+    want = {"f32": torch.complex64, "f64": torch.complex128}
+    if prec not in want:
+        raise ValueError(f"fse_mass_noalloc: prec must be 'f32' or 'f64', not {prec!r}")
+    if not (isinstance(psi, torch.Tensor) and psi.is_cuda and psi.is_contiguous() and psi.dtype == want[prec]):
+        raise ValueError(f"fse_mass_noalloc: psi must be a contiguous CUDA {want[prec]} tensor")
+    if not (isinstance(mass_out, torch.Tensor) and mass_out.is_cuda and mass_out.dtype == torch.float64
+            and mass_out.numel() >= 1 and mass_out.device == psi.device):
+        raise ValueError("fse_mass_noalloc: mass_out must be a float64 CUDA tensor on psi's device")
+    npoints = int(npoints)
+    if not 0 <= npoints <= psi.numel():
+        raise ValueError(f"fse_mass_noalloc: npoints {npoints} outside [0, {psi.numel()}]")
+    st = load().fse_mass_noalloc(_ptr(psi), PRECS[prec], npoints, float(cell_volume), _ptr(mass_out),
                                  ct.c_void_p(stream or 0))
     _check(st, "fse_mass_noalloc")
 

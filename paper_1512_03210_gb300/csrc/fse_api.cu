@@ -27,7 +27,7 @@ cudaError_t launch_gs_axis(double* g, double* cs, double* ynode, double* ywt, co
                            double W, int n, cudaStream_t st);
 template <typename Real>
 cudaError_t launch_chat(void* out, const double* w, const double* gx, const double* gy,
-                        const double* gz, int Q, int nx, int ny, int nz, int dim, double dkx,
+                        const double* gz, int Q, int nx, int ny, int nz, int cx, int dim, double dkx,
                         double dky, double dkz, double I0, double I2, cudaStream_t st);
 }  // namespace fse
 
@@ -354,15 +354,16 @@ fse_status nonlocal_yz(fse_plan* P, void* spec, double ta, double tb, bool integ
   m.lx = 2 * P->nx;
   m.dkx = 2 * kPi / (2.0 * (P->p.hi[0] - P->p.lo[0]));
   m.chat = P->ws_ptr(P->off_chat);
-  m.chat_sp = P->nx + 1;
-  m.chat_sr = (long long)(P->nx + 1) * (P->ny + 1);
+  m.chat_cx = P->chat_cx;
+  m.chat_sp = P->chat_cx;
+  m.chat_sr = (long long)P->chat_cx * (P->ny + 1);
   fse_status st;
   if (P->dim == 2) {
     m.lp = 0;
     m.lr = 2 * P->ny;
     m.dkr = 2 * kPi / (2.0 * (P->p.hi[1] - P->p.lo[1]));
     m.chat_sp = 0;
-    m.chat_sr = P->nx + 1;
+    m.chat_sr = P->chat_cx;
     m.scale = extra_scale / (4.0 * P->nx * P->ny);
     if (m.mode == MUL_COULOMB) {
       m.a0 = d * m.scale;
@@ -404,6 +405,47 @@ fse_status nonlocal_yz(fse_plan* P, void* spec, double ta, double tb, bool integ
   ColArgs ah{spec, (long long)2 * P->ny * P->sx, P->sx, P->nz, P->nx + 1, 2 * P->ny, P->ny,
              tiles(P, 2 * P->ny, P->nx + 1)};
   return col(P, FSE_PASS_PAD, 2 * P->ny, COL_CROPI, with_tail(P, ah, 2 * P->ny), m);
+}
+
+// Host-side checks of one parameter set (shared by fse_plan_create and
+// fse_batch_create): ranges of Eq. SFSE and Eq. Kernel, supported sizes,
+// finite scalars.
+fse_status validate_params(const fse_params& p) {
+  if (p.dim != 2 && p.dim != 3) return FSE_ERR_INVALID;
+  if (!(p.s > 0.0) || !std::isfinite(p.s) || !(p.m >= 0.0) || !std::isfinite(p.m)) return FSE_ERR_INVALID;
+  if (p.dt == 0.0 || !std::isfinite(p.dt)) return FSE_ERR_INVALID;
+  if (!std::isfinite(p.omega) || !std::isfinite(p.beta) || !std::isfinite(p.lambda)) return FSE_ERR_INVALID;
+  if (p.kernel < FSE_KERNEL_NONE || p.kernel > FSE_KERNEL_DDI2D) return FSE_ERR_INVALID;
+  if (p.kernel == FSE_KERNEL_DDI3D && p.dim != 3) return FSE_ERR_INVALID;
+  if (p.kernel == FSE_KERNEL_DDI2D && (p.dim != 2 || p.mu != 1.0)) return FSE_ERR_INVALID;
+  if (p.prec != FSE_F32 && p.prec != FSE_F64) return FSE_ERR_INVALID;
+  for (int j = 0; j < p.dim; ++j) {
+    if (!std::isfinite(p.lo[j]) || !std::isfinite(p.hi[j]) || !(p.hi[j] > p.lo[j])) return FSE_ERR_INVALID;
+    if (!std::isfinite(p.gamma[j])) return FSE_ERR_INVALID;
+    if (!size_supported(p.n[j])) return FSE_ERR_UNSUPPORTED;
+  }
+  for (int j = 0; j < 3; ++j)
+    if (!std::isfinite(p.dip_n[j]) || !std::isfinite(p.lat_k[j])) return FSE_ERR_INVALID;
+  if (p.kernel == FSE_KERNEL_COULOMB && !(p.mu > 0.0 && p.mu <= p.dim - 1)) return FSE_ERR_INVALID;
+  if (p.kernel == FSE_KERNEL_DDI3D && p.mu != 1.0) return FSE_ERR_INVALID;
+  if (!std::isfinite(p.gs_delta) || !std::isfinite(p.gs_h) || !std::isfinite(p.gs_tmin)) return FSE_ERR_INVALID;
+  if (p.renormalize != 0 && p.renormalize != 1) return FSE_ERR_INVALID;
+  if (p.order != 0 && p.order != 2 && p.order != 4) return FSE_ERR_INVALID;
+  if (!std::isfinite(p.lat_amp) || p.quad_nodes < 0 || p.quad_nodes > 16) return FSE_ERR_INVALID;
+  return FSE_OK;
+}
+
+// The parameter set with the documented defaults filled in (0 = default).
+fse_params effective_params(const fse_params& in) {
+  fse_params p = in;
+  if (p.gs_delta <= 0) p.gs_delta = 1e-3;
+  if (p.gs_h <= 0) p.gs_h = 0.125;
+  if (p.kernel == FSE_KERNEL_NONE) p.mu = 1.0;
+  if (p.order == 0) p.order = 2;
+  if (p.quad_nodes == 0) p.quad_nodes = 8;
+  // the dropped tail of the sinc quadrature is ~ e^{mu t_min} / mu
+  if (p.gs_tmin == 0) p.gs_tmin = -36.0 / p.mu;
+  return p;
 }
 
 bool has_nonlocal(const fse_plan* P) { return P->p.kernel != FSE_KERNEL_NONE && P->p.lambda != 0.0; }
@@ -486,33 +528,11 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
   *out = nullptr;
   *ws_bytes = 0;
   const fse_params& p = *prm;
-  if (p.dim != 2 && p.dim != 3) return FSE_ERR_INVALID;
-  if (!(p.s > 0.0) || !(p.m >= 0.0) || p.dt == 0.0 || !std::isfinite(p.dt)) return FSE_ERR_INVALID;
-  if (p.kernel < FSE_KERNEL_NONE || p.kernel > FSE_KERNEL_DDI2D) return FSE_ERR_INVALID;
-  if (p.kernel == FSE_KERNEL_DDI3D && p.dim != 3) return FSE_ERR_INVALID;
-  if (p.kernel == FSE_KERNEL_DDI2D && (p.dim != 2 || p.mu != 1.0)) return FSE_ERR_INVALID;
-  if (p.prec != FSE_F32 && p.prec != FSE_F64) return FSE_ERR_INVALID;
-  for (int j = 0; j < p.dim; ++j) {
-    if (!(p.hi[j] > p.lo[j])) return FSE_ERR_INVALID;
-    if (!size_supported(p.n[j])) return FSE_ERR_UNSUPPORTED;
-  }
-  if (p.kernel == FSE_KERNEL_COULOMB && !(p.mu > 0.0 && p.mu <= p.dim - 1)) return FSE_ERR_INVALID;
-  if (p.kernel == FSE_KERNEL_DDI3D && p.mu != 1.0) return FSE_ERR_INVALID;
-  if (p.renormalize != 0 && p.renormalize != 1) return FSE_ERR_INVALID;
-  if (p.order != 0 && p.order != 2 && p.order != 4) return FSE_ERR_INVALID;
-  if (!std::isfinite(p.lat_amp) || p.quad_nodes < 0 || p.quad_nodes > 16) return FSE_ERR_INVALID;
-  for (int j = 0; j < 3; ++j)
-    if (!std::isfinite(p.lat_k[j])) return FSE_ERR_INVALID;
+  const fse_status vst = validate_params(p);
+  if (vst != FSE_OK) return vst;
   fse_plan* P = new (std::nothrow) fse_plan();
   if (!P) return FSE_ERR_NOMEM;
-  P->p = p;
-  if (P->p.gs_delta <= 0) P->p.gs_delta = 1e-3;
-  if (P->p.gs_h <= 0) P->p.gs_h = 0.125;
-  if (P->p.kernel == FSE_KERNEL_NONE) P->p.mu = 1.0;
-  if (P->p.order == 0) P->p.order = 2;
-  if (P->p.quad_nodes == 0) P->p.quad_nodes = 8;
-  // the dropped tail of the sinc quadrature is ~ e^{mu t_min} / mu
-  if (P->p.gs_tmin == 0) P->p.gs_tmin = -36.0 / P->p.mu;
+  P->p = effective_params(p);
   P->stream = reinterpret_cast<cudaStream_t>(stream);
   cudaGetDevice(&P->device);
   P->dim = p.dim;
@@ -524,6 +544,7 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
   P->csize = 2 * P->rsize;
   for (int j = 0; j < 3; ++j) P->h[j] = j < p.dim ? (p.hi[j] - p.lo[j]) / p.n[j] : 0.0;
   P->sx = ((P->nx + 1 + 15) / 16) * 16;
+  P->chat_cx = ((P->nx + 1 + 3) / 4) * 4;
 
   // Gaussian-sum nodes (Eq. GS-Gene): sinc quadrature of
   // r^-mu = (2 / Gamma(mu/2)) int exp(mu t - r^2 e^{2t}) dt in unit-box units, scaled.
@@ -572,7 +593,7 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
     off = align256(off + 2 * (size_t)lens[i] * P->csize);  // (cos, sin) and modulus correction
   }
   P->off_chat = off;
-  const size_t nchat = (size_t)(P->nx + 1) * (P->ny + 1) * (p.dim == 3 ? P->nz + 1 : 1);
+  const size_t nchat = (size_t)P->chat_cx * (P->ny + 1) * (p.dim == 3 ? P->nz + 1 : 1);
   off = align256(off + nchat * P->rsize);
   const size_t kin_elems = (size_t)(P->nx / 2 + 1) * (P->ny / 2 + 1) * (p.dim == 3 ? P->nz / 2 + 1 : 1);
   P->off_kin_half = off;
@@ -694,10 +715,10 @@ fse_status fse_kernel_precompute(fse_plan_t P) {
     e = P->prec == FSE_F32
             ? launch_chat<float>(P->ws_ptr(P->off_chat), dw, reinterpret_cast<double*>(base + P->pre_g[0]),
                                  reinterpret_cast<double*>(base + P->pre_g[1]), gz, Q, P->nx, P->ny, P->nz,
-                                 P->dim, dk[0], dk[1], dk[2], P->I0, P->I2, P->stream)
+                                 P->chat_cx, P->dim, dk[0], dk[1], dk[2], P->I0, P->I2, P->stream)
             : launch_chat<double>(P->ws_ptr(P->off_chat), dw, reinterpret_cast<double*>(base + P->pre_g[0]),
                                   reinterpret_cast<double*>(base + P->pre_g[1]), gz, Q, P->nx, P->ny, P->nz,
-                                  P->dim, dk[0], dk[1], dk[2], P->I0, P->I2, P->stream);
+                                  P->chat_cx, P->dim, dk[0], dk[1], dk[2], P->I0, P->I2, P->stream);
     if (launched(P, e, "kernel transform") != FSE_OK) return FSE_ERR_CUDA;
   }
   P->precomputed = true;

@@ -186,8 +186,18 @@ fse_status fse_batch_create(const fse_params* runs, int nruns, void* stream, fse
   if (!runs || nruns <= 0 || !out || !workspace_bytes) return FSE_ERR_INVALID;
   *out = nullptr;
   *workspace_bytes = 0;
+  const fse_params e0 = effective_params(runs[0]);
   for (int r = 0; r < nruns; ++r) {
     const fse_params& p = runs[r];
+    // every run gets the checks of fse_plan_create (only the first run of a
+    // size group builds a plan)
+    const fse_status vst = validate_params(p);
+    if (vst != FSE_OK) return vst;
+    // the group's kernel transform is built from its first run: the exponent
+    // and the Gaussian-sum fit must be the same for every run
+    const fse_params e = effective_params(p);
+    if (e.mu != e0.mu || e.gs_delta != e0.gs_delta || e.gs_h != e0.gs_h || e.gs_tmin != e0.gs_tmin)
+      return FSE_ERR_UNSUPPORTED;
     if (p.dim != 2 || p.prec != FSE_F32 || p.renormalize != 0 || (p.order != 0 && p.order != 2) ||
         p.lat_amp != 0.0)
       return FSE_ERR_UNSUPPORTED;
@@ -350,7 +360,8 @@ fse_status fse_batch_step(fse_batch_t B, void* const* psi, double t0, int nsteps
     mk2.lx = 2 * P->nx;
     mk2.lr = 2 * P->ny;
     mk2.chat = P->ws_ptr(P->off_chat);
-    mk2.chat_sr = P->nx + 1;
+    mk2.chat_cx = P->chat_cx;
+    mk2.chat_sr = P->chat_cx;
     mk2.scale = 1.0 / (4.0 * P->nx * P->ny);
     ColArgs cg{nullptr, 0, P->sx, 1, P->nx + 1, P->ny, P->ny, tiles(P, 2 * P->ny, P->nx + 1)};
     auto chk = [&](cudaError_t ee, const char* w) -> fse_status {

@@ -17,6 +17,7 @@ struct fse_plan {
   size_t rsize = 4, csize = 8;
   double h[3] = {0, 0, 0};
   long long sx = 0;  // row stride of the padded density spectrum S (elements)
+  int chat_cx = 0;   // row stride of the C^ octant: nx + 1 rounded up to a multiple of 4 (16-byte rows)
 
   // Gaussian-sum fit (Eq. GS-Gene) and near-field integrals (Eq. taylor), float64 on the host
   std::vector<double> gs_w, gs_tau, gl_x, gl_w;
@@ -66,6 +67,8 @@ fse_status kinetic_yz(fse_plan* P, void* psi, double f, double dt);
 fse_status nonlocal_yz(fse_plan* P, void* spec, double ta, double tb, bool integrated, const double* mdir,
                        double extra_scale);
 bool has_nonlocal(const fse_plan* P);
+fse_status validate_params(const fse_params& p);
+fse_params effective_params(const fse_params& p);
 void trap_coefficients(const fse_plan* P, double ta, double tb, const double* gam, double out[4]);
 void dipole_matrix(const fse_plan* P, double ta, double tb, double M[6]);
 fse_status run_steps(fse_plan* P, void* psi, double t0, int nsteps, const double* gps);

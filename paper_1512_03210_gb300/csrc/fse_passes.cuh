@@ -74,6 +74,7 @@ struct MulArgs {
   double q[6];       // DDI: 3*scale*(Mxx, Myy, Mrr..): see host code (x, plane, row)
   const void* chat;
   long long chat_sp, chat_sr;
+  int chat_cx;       // padded length of a C^ row (x bins 0..lx/2, then zeros), a multiple of 4
   const void* kin;   // kinetic: octant table of exp(-i f theta_k) on |p_j| = 0..n_j/2
   long long kin_sp, kin_sr;  // kinetic: octant strides of the plane and row axes
   int conj;          // kinetic: multiply by the conjugate of the table (adjoint)
@@ -275,7 +276,9 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const MulArgs& m,
 #pragma unroll
   for (int q = 0; q < CW; ++q) {
     my_ok[q] = col_of(cg * CW + q, my_plane[q], my_px[q]);
-    colp[q] = reinterpret_cast<C*>(a.data) + (long long)my_plane[q] * a.plane_stride + my_px[q];
+    // the columns of a full tile are adjacent in one plane
+    colp[q] = (!gather && q > 0) ? colp[0] + q
+                                 : reinterpret_cast<C*>(a.data) + (long long)my_plane[q] * a.plane_stride + my_px[q];
   }
   // both columns of a pair side by side in memory, 16-byte aligned: one access per row
   bool vec = false;
@@ -288,13 +291,22 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const MulArgs& m,
     // start fetching C^ (|p_row| = 0..N/2, this tile's columns) while the forward transform runs
     const Real* ch = reinterpret_cast<const Real*>(m.chat);
     if (!gather) {
+      // the tile's columns of a C^ row are contiguous and 16-byte aligned
+      // (rows padded to a multiple of 4 values, c0 a multiple of NCOL): one
+      // 16-byte copy per EPC values; copies past the padded row are zero-filled
+      constexpr int EPC = 16 / (int)sizeof(Real), CPR = NCOL / EPC;
+      static_assert(NCOL % EPC == 0, "C^ copies of 16 bytes");
       const Real* chp = ch + (m.lp ? (long long)abs(wrap_index(plane, m.lp)) * m.chat_sp : 0) + c0;
-      for (int idx = tid; idx < (N / 2 + 1) * NCOL; idx += NT) {
-        const int ar = idx / NCOL, cc = idx % NCOL;
-        if (c0 + cc < a.ncols && c0 + cc <= (m.lx >> 1))
-          cp_async<sizeof(Real)>(&sC[idx], &chp[(long long)ar * m.chat_sr + cc]);
-        else
-          sC[idx] = Real(0);
+      const int left = m.chat_cx - c0;
+      for (int idx = tid; idx < (N / 2 + 1) * CPR; idx += NT) {
+        const int ar = idx / CPR, qd = idx - ar * CPR;
+        Real* dst = &sC[ar * NCOL + qd * EPC];
+        if (qd * EPC < left) {
+          cp_async<16>(dst, &chp[(long long)ar * m.chat_sr + qd * EPC]);
+        } else {
+#pragma unroll
+          for (int e = 0; e < EPC; ++e) dst[e] = Real(0);
+        }
       }
     } else {
       for (int idx = tid; idx < (N / 2 + 1) * NCOL; idx += NT) {
@@ -360,12 +372,18 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const MulArgs& m,
         for (int r = 0; r < RL; ++r) {
           const int row = j + r * (N / RL);
           const long long ro = (long long)abs(wrap_index(row, m.lr)) * m.kin_sr;
+          C y[CW];
 #pragma unroll
           for (int q = 0; q < CW; ++q) {
             const C t = my_ok[q] ? __ldg(&tab[q][ro + ax[q]]) : mk(Real(1), Real(0));
             const C x = unit_mul(v[(i * CW + q) * RL + r], t.x, t.y, m.conj != 0);
-            if constexpr (FUSED) v[(i * CW + q) * RL + r] = mk(sc * x.x, sc * x.y);
-            else buf[row * LDS + cg * CW + q] = mk(sc * x.x, sc * x.y);
+            y[q] = mk(sc * x.x, sc * x.y);
+            if constexpr (FUSED) v[(i * CW + q) * RL + r] = y[q];
+          }
+          // both columns of a pair in one 16-byte store (LDS even)
+          if constexpr (!FUSED) {
+            if constexpr (CW == 2) st_pair(&buf[row * LDS + cg * CW], y[0], y[1]);
+            else buf[row * LDS + cg] = y[0];
           }
         }
       }
@@ -396,9 +414,18 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const MulArgs& m,
           const int pr = wrap_index(row, m.lr);
           const Real kr = prm<Real>(m.dkr, m.f.dkr) * Real(pr);
           const Real kro = (2 * row == m.lr) ? Real(0) : kr;
+          Real cvq[CW];
+          C yq[CW];
+          if constexpr (CW == 2) {
+            const auto c2 = *reinterpret_cast<const typename Cplx<Real>::T*>(&sC[abs(pr) * NCOL + cg * CW]);
+            cvq[0] = c2.x;
+            cvq[1] = c2.y;
+          } else {
+            cvq[0] = sC[abs(pr) * NCOL + cg];
+          }
 #pragma unroll
           for (int q = 0; q < CW; ++q) {
-            const Real cv = sC[abs(pr) * NCOL + cg * CW + q];
+            const Real cv = cvq[q];
             Real f;
             if (ddi) {
               const Real qf = Aq[q] + Bq[q] * kro + prm<Real>(m.q[2], m.f.q[2]) * kr * kr;
@@ -407,8 +434,12 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const MulArgs& m,
               f = prm<Real>(m.a0, m.f.a0) * cv;
             }
             const C x = v[(i * CW + q) * RL + r];
-            if constexpr (FUSED) v[(i * CW + q) * RL + r] = mk(f * x.x, f * x.y);
-            else buf[row * LDS + cg * CW + q] = mk(f * x.x, f * x.y);
+            yq[q] = mk(f * x.x, f * x.y);
+            if constexpr (FUSED) v[(i * CW + q) * RL + r] = yq[q];
+          }
+          if constexpr (!FUSED) {
+            if constexpr (CW == 2) st_pair(&buf[row * LDS + cg * CW], yq[0], yq[1]);
+            else buf[row * LDS + cg] = yq[0];
           }
         }
       }
@@ -832,6 +863,11 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
       if (tid == 0) a.part[bid] = acc;
       return;
     } else {
+      // optional renormalisation factor, read and converted once per thread: a
+      // conversion from double inside the element loop issues on the narrow
+      // FP64 pipe for every element, even where the branch is predicated off
+      const bool rescale = a.scale != nullptr;
+      const Real fsc = rescale ? Real(*a.scale) : Real(1);
       __syncthreads();
 #pragma unroll
       for (int it = 0; it < PER; ++it) {
@@ -850,10 +886,7 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
             Real sn, cs;
             phase_sincos(th, &sn, &cs);
             u2 = unit_mul(u, cs, -sn, false);
-            if (a.scale) {
-              const Real f = Real(*a.scale);
-              u2 = mk(f * u2.x, f * u2.y);
-            }
+            if (rescale) u2 = mk(fsc * u2.x, fsc * u2.y);
           }
           buf[x * LDS + l] = u2;
         }

@@ -129,10 +129,12 @@ __global__ void k_gs_table(double* g, const double* cs, const double* ynode, con
   }
 }
 
-// C^ on the octant [nz+1][ny+1][nx+1] (dim 3) or [ny+1][nx+1] (dim 2).
+// C^ on the octant [nz+1][ny+1][cx] (dim 3) or [ny+1][cx] (dim 2): x bins
+// 0..nx, then zeros up to the row stride cx (a multiple of 4, so that every
+// row starts 16-byte aligned).
 template <typename Real>
 __global__ void k_chat(Real* out, const double* w, const double* gx, const double* gy,
-                       const double* gz, int Q, int nx, int ny, int nz, int dim, double dkx,
+                       const double* gz, int Q, int nx, int ny, int nz, int cx, int dim, double dkx,
                        double dky, double dkz, double I0, double I2) {
   const int px = blockIdx.x * blockDim.x + threadIdx.x;
   const int py = blockIdx.y;
@@ -144,12 +146,16 @@ __global__ void k_chat(Real* out, const double* w, const double* gx, const doubl
     wyz[q] = v;
   }
   __syncthreads();
-  if (px > nx) return;
+  if (px >= cx) return;
+  if (px > nx) {
+    out[((long long)pz * (ny + 1) + py) * cx + px] = Real(0);
+    return;
+  }
   double acc = 0.0;
   for (int q = 0; q < Q; ++q) acc = fma(wyz[q], gx[(long long)q * (nx + 1) + px], acc);
   const double kx = dkx * px, ky = dky * py, kz = dim == 3 ? dkz * pz : 0.0;
   acc += I0 - I2 * (kx * kx + ky * ky + kz * kz) / (2.0 * dim);
-  out[((long long)pz * (ny + 1) + py) * (nx + 1) + px] = Real(acc);
+  out[((long long)pz * (ny + 1) + py) * cx + px] = Real(acc);
 }
 
 template <typename Real>
@@ -177,22 +183,22 @@ cudaError_t launch_gs_axis(double* g, double* cs, double* ynode, double* ywt, co
 
 template <typename Real>
 cudaError_t launch_chat(void* out, const double* w, const double* gx, const double* gy,
-                        const double* gz, int Q, int nx, int ny, int nz, int dim, double dkx,
+                        const double* gz, int Q, int nx, int ny, int nz, int cx, int dim, double dkx,
                         double dky, double dkz, double I0, double I2, cudaStream_t st) {
-  dim3 grid((nx + 1 + 127) / 128, ny + 1, dim == 3 ? nz + 1 : 1);
+  dim3 grid((cx + 127) / 128, ny + 1, dim == 3 ? nz + 1 : 1);
   const size_t smem = sizeof(double) * (size_t)Q;
   k_chat<Real><<<grid, 128, smem, st>>>(reinterpret_cast<Real*>(out), w, gx, gy, gz, Q, nx, ny, nz,
-                                        dim, dkx, dky, dkz, I0, I2);
+                                        cx, dim, dkx, dky, dkz, I0, I2);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_twiddles<float>(void*, int, cudaStream_t);
 template cudaError_t launch_twiddles<double>(void*, int, cudaStream_t);
 template cudaError_t launch_chat<float>(void*, const double*, const double*, const double*,
-                                        const double*, int, int, int, int, int, double, double,
+                                        const double*, int, int, int, int, int, int, double, double,
                                         double, double, double, cudaStream_t);
 template cudaError_t launch_chat<double>(void*, const double*, const double*, const double*,
-                                         const double*, int, int, int, int, int, double, double,
+                                         const double*, int, int, int, int, int, int, double, double,
                                          double, double, double, cudaStream_t);
 
 }  // namespace fse

@@ -95,3 +95,50 @@ def test_set_workspace_checks_size_and_alignment():
         assert "precompute" in fse.fse_plan_error(h)
     finally:
         lib.fse_plan_destroy(h)
+
+
+def test_plan_rejects_non_finite_scalars():
+    good = I.workload("2d_coulomb_128")
+    nan = float("nan")
+    for key, val in (("beta", nan), ("omega", float("inf")), ("lam", nan), ("gamma", (1.0, nan)),
+                     ("s", float("inf")), ("lo", (-8.0, nan))):
+        assert _create(dict(good, **{key: val}))[0] == 1, key
+
+
+def _batch_create(runs):
+    lib = fse.load()
+    arr = (fse.FseParams * len(runs))(*[fse.to_params(r) for r in runs])
+    h = ct.c_void_p()
+    nb = ct.c_size_t()
+    st = lib.fse_batch_create(arr, len(runs), None, ct.byref(h), ct.byref(nb))
+    if h.value:
+        lib.fse_batch_destroy(h)
+    return st
+
+
+def test_batch_validates_every_run():
+    """Every run of a batch gets fse_plan_create's checks, not only the first of
+    each size group, and runs that would need another kernel transform (mu,
+    Gaussian-sum fit) than the group's first run are refused."""
+    runs = I.batched_runs(6)
+    assert _batch_create(runs) == 0
+    bad = [dict(r) for r in runs]
+    bad[3]["s"] = -0.5
+    assert _batch_create(bad) == 1
+    bad = [dict(r) for r in runs]
+    bad[4]["beta"] = float("nan")
+    assert _batch_create(bad) == 1
+    bad = [dict(r) for r in runs]
+    bad[5]["dt"] = float("inf")
+    assert _batch_create(bad) == 1
+    mixed = [dict(r) for r in runs]
+    mixed[2]["mu"] = 0.5
+    assert _batch_create(mixed) == 2
+    mixed = [dict(r) for r in runs]
+    mixed[1]["gs_h"] = 0.1
+    assert _batch_create(mixed) == 2
+    # explicit defaults are the same fit as the zero defaults
+    same = [dict(r) for r in runs]
+    same[1]["gs_h"] = 0.125
+    same[2]["gs_delta"] = 1e-3
+    assert _batch_create(same) == 0

@@ -7,6 +7,7 @@ import pytest
 
 import fse_inputs as I
 import oracle as O
+from tolerances import assert_parity, bounds
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -58,7 +59,7 @@ def test_batch_matches_oracle(lib):
     for d, p0, x in zip(runs, psis, xs):
         ref = O.evolve(p0, O.params(d), 0.0, 4)
         got = x.cpu().numpy().astype(np.complex128)
-        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 4 * 5e-6
+        assert_parity(got, ref, *bounds("f32", 4), f"batch run n={d['n'][0]}")
 
 
 def test_batched_workload_draws(lib):
@@ -72,3 +73,36 @@ def test_batched_workload_draws(lib):
         h = np.prod([(d["hi"][j] - d["lo"][j]) / d["n"][j] for j in range(2)])
         m = float((x.abs().double() ** 2).sum()) * h
         assert abs(m - 1.0) < 1e-5
+
+
+def _one_run_per_size():
+    """The first run of each grid size among the batched workload's draws."""
+    seen, out = set(), []
+    for r in I.batched_runs():
+        if r["n"][0] not in seen:
+            seen.add(r["n"][0])
+            out.append(r)
+    return sorted(out, key=lambda r: r["n"][0])
+
+
+def test_batch_workload_sizes_match_oracle(lib):
+    """One run of each workload size (128, 192, 256, 384, 512; radix-3 plans at
+    192 and 384) advanced together in one batch for 3 steps: each run within the
+    float32 bounds of the FP64 oracle, element by element, and bit-identical to
+    the same run advanced alone."""
+    runs = _one_run_per_size()
+    assert [r["n"][0] for r in runs] == [128, 192, 256, 384, 512]
+    psis = [I.psi0(r) for r in runs]
+    b = lib.Batch(runs)
+    xs = b.to_device(psis)
+    b.step(xs, 0.0, 3)
+    torch.cuda.synchronize()
+    for d, p0, x in zip(runs, psis, xs):
+        ref = O.evolve(p0, O.params(d), 0.0, 3)
+        got = x.cpu().numpy().astype(np.complex128)
+        assert_parity(got, ref, *bounds("f32", 3), f"batched workload run n={d['n'][0]}")
+        plan = lib.Plan(d)
+        y = plan.to_device(p0)
+        plan.step(y, 0.0, 3)
+        torch.cuda.synchronize()
+        assert torch.equal(x, y)

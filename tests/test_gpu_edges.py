@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 import oracle as O
+from tolerances import assert_parity, bounds
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -101,4 +102,4 @@ def test_mixed_radix_2d_f32(lib, n):
     x = plan.to_device(psi0)
     plan.step(x, 0.0, 3)
     torch.cuda.synchronize()
-    assert _rel(x.cpu().numpy().astype(np.complex128), ref) < 5e-6 * 3
+    assert_parity(x.cpu().numpy().astype(np.complex128), ref, *bounds("f32", 3), f"mixed radix {n}")
