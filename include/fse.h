@@ -235,8 +235,14 @@ fse_status fse_batch_set_workspace(fse_batch_t batch, void* dev_ptr, size_t byte
 fse_status fse_batch_precompute(fse_batch_t batch);
 /* Advance every run by nsteps steps from t0. psi is a HOST array of nruns
  * DEVICE pointers, one wave function per run in that run's layout [ny][nx]
- * (float2). Asynchronous. Errors: FSE_ERR_INVALID (null or misaligned
- * pointers, precompute not run). */
+ * (float2). The first call with a given nsteps captures its launches (every
+ * size group on a stream of its own) into a CUDA graph, on a stream the batch
+ * owns; later calls with that nsteps only upload the pointers and t0 and
+ * replay the graph. The capture uses thread-local mode, so the first call with
+ * a new nsteps must not be made while this thread captures another stream.
+ * Asynchronous, ordered on the batch's stream. Errors: FSE_ERR_INVALID (null
+ * or misaligned pointers, precompute not run), FSE_ERR_CUDA (capture or
+ * launch failure). */
 fse_status fse_batch_step(fse_batch_t batch, void* const* psi, double t0, int nsteps);
 /* Release the batch's host memory (never the workspace). */
 fse_status fse_batch_destroy(fse_batch_t batch);
@@ -272,9 +278,12 @@ typedef struct {
  * its Krylov vectors on this plan: ten complex and three real fields. */
 fse_status fse_ground_state_workspace(fse_plan_t plan, size_t* bytes);
 /* psi (device, plan layout): initial guess on entry (scaled to unit mass),
- * the last iterate on return. The call synchronises the plan's stream (the
- * Krylov scalars are read on the host) and uses the plan's scratch field and
- * spectrum. info (nullable) receives the counts. Errors: FSE_ERR_INVALID (null
+ * the last iterate on return. The BiCGStab scalars stay on the device; the
+ * host reads them one iteration behind the GPU (so one extra, idempotent
+ * iteration may run after convergence) and the call returns with the plan's
+ * stream synchronised. It uses the plan's scratch field and spectrum, and
+ * keeps 256 bytes of page-locked host memory and two events on the plan
+ * (released by fse_plan_destroy). info (nullable) receives the counts. Errors: FSE_ERR_INVALID (null
  * or misaligned buffers, precompute not run, dt <= 0, negative counts or
  * tolerances, zero initial field), FSE_ERR_NOMEM (workspace too small),
  * FSE_ERR_NONFINITE (the iteration produced a non-finite field). */

@@ -11,12 +11,15 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libfse.so")
+# arithmetic-throughput probes used by the benchmark's roofline (not the solver)
+PEAKS_SRC = "fse_peaks.cu"
+PEAKS_LIB = os.path.join(OUT, "libfse_peaks.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["fse_api.cu", "fse_precompute.cu", "fse_observables.cu", "fse_adjoint.cu",
            "fse_col_f32.cu", "fse_col_f64.cu", "fse_x_f32.cu", "fse_x_f64.cu", "fse_noalloc.cu",
            "fse_batch.cu", "fse_ground.cu"]
-HEADERS = ["fse_fft.cuh", "fse_passes.cuh", "fse_launch.cuh", "fse_internal.h"]
+HEADERS = ["fse_fft.cuh", "fse_fft_x2.cuh", "fse_passes.cuh", "fse_launch.cuh", "fse_internal.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
@@ -53,6 +56,12 @@ def build(verbose: bool = False, force: bool = False) -> str:
             if verbose:
                 print(" ".join(cmd), flush=True)
             procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    peaks_src = os.path.join(CSRC, PEAKS_SRC)
+    if force or _stale(PEAKS_LIB, [peaks_src]):
+        cmd = [nvcc, *ARCH, *FLAGS, "-shared", "-cudart", "shared", peaks_src, "-o", PEAKS_LIB]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        procs.append((PEAKS_SRC, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
     failed = []
     for src, p in procs:
         out, _ = p.communicate()
@@ -63,7 +72,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    if force or procs or not os.path.exists(LIB):
+    if force or any(src != PEAKS_SRC for src, _ in procs) or not os.path.exists(LIB):
         cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
         cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", LIB, *objs,
                "-Xlinker", f"-rpath,{cuda_lib}"]

@@ -590,7 +590,9 @@ fse_status fse_plan_create(const fse_params* prm, void* stream, fse_plan_t* out,
     if (seen) continue;
     P->tw_len.push_back(lens[i]);
     P->tw_off.push_back(off);
-    off = align256(off + 2 * (size_t)lens[i] * P->csize);  // (cos, sin) and modulus correction
+    // (cos, sin) and remainder; float plans also hold their (c, c, s, s)
+    // broadcast copy for the packed column passes
+    off = align256(off + 2 * (size_t)lens[i] * P->csize + (P->prec == FSE_F32 ? 2 * (size_t)lens[i] * 16 : 0));
   }
   P->off_chat = off;
   const size_t nchat = (size_t)P->chat_cx * (P->ny + 1) * (p.dim == 3 ? P->nz + 1 : 1);
@@ -783,6 +785,9 @@ fse_status fse_plan_destroy(fse_plan_t P) {
     cudaEventDestroy(r.b);
   }
   for (auto e : P->ev_pool) cudaEventDestroy(e);
+  for (auto e : P->gs_ev)
+    if (e) cudaEventDestroy(e);
+  if (P->gs_host) cudaFreeHost(P->gs_host);
   delete P;
   return FSE_OK;
 }

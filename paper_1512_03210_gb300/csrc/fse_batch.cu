@@ -6,7 +6,10 @@
 // parameters (s through its kinetic tables, Omega, beta, lambda, dt, gamma)
 // come from a device descriptor table. The pass bodies are the single-run
 // ones, so a run advanced in a batch is bit-identical to the same run
-// advanced alone. Runs never wait on one another.
+// advanced alone. Runs never wait on one another. The launches of a call of
+// nsteps steps are captured once as a CUDA graph (per step count) and replayed
+// by later calls; the call's data (wave-function pointers, start time) reach
+// the kernels through device tables uploaded ahead of each replay.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -53,13 +56,15 @@ k_colpass_batch(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__
 template <typename Real, int NX, int KIND>
 __global__ void __launch_bounds__(XCfg<Real, NX>::NT, XCfg<Real, NX>::MINB)
 k_xpass_batch(XArgs a, const typename Cplx<Real>::T* __restrict__ twn, const typename Cplx<Real>::T* __restrict__ tw2n,
-              const BatchRun* runs, double t0, int step) {
+              const BatchRun* runs, const double* t0p, int step) {
   const BatchRun r = runs[blockIdx.y];
   a.psi = r.psi;
   a.spec = a.use_spec ? r.spec : nullptr;
   if constexpr (KIND == XP_A) {
-    // exact time integral of the rotating harmonic trap over the run's step (Eq. int_poten)
-    const double ta = t0 + step * r.dt, d = r.dt, mid = 2.0 * ta + d;
+    // exact time integral of the rotating harmonic trap over the run's step
+    // (Eq. int_poten); the call's start time t0 is a device scalar, so that a
+    // captured graph of the step sequence serves every call
+    const double ta = *t0p + step * r.dt, d = r.dt, mid = 2.0 * ta + d;
     const double C2 = cos(r.omega * mid) * sin_over_dev(r.omega, d);
     const double S2 = sin(r.omega * mid) * sin_over_dev(r.omega, d);
     a.pa = 0.25 * (r.gx2 * (d + C2) + r.gy2 * (d - C2));
@@ -104,8 +109,8 @@ static cudaError_t launch_colb(int N, int mode, const ColArgs& a, const MulArgs&
 }
 
 template <int NX, int KIND>
-static cudaError_t xb(const XArgs& a, const void* twn, const void* tw2n, const BatchRun* runs, int nr, double t0,
-                      int step, cudaStream_t st) {
+static cudaError_t xb(const XArgs& a, const void* twn, const void* tw2n, const BatchRun* runs, int nr,
+                      const double* t0, int step, cudaStream_t st) {
   typedef XCfg<float, NX> K;
   const size_t smem = K::smem_bytes();
   static std::atomic<unsigned long long> done{0};
@@ -120,7 +125,7 @@ static cudaError_t xb(const XArgs& a, const void* twn, const void* tw2n, const B
 }
 
 static cudaError_t launch_xb(int kind, int nx, const XArgs& a, const void* twn, const void* tw2n,
-                             const BatchRun* runs, int nr, double t0, int step, cudaStream_t st) {
+                             const BatchRun* runs, int nr, const double* t0, int step, cudaStream_t st) {
   switch (nx) {
 #define FSE_CASE(n)                                                    \
   case n:                                                              \
@@ -168,6 +173,18 @@ struct fse_batch {
   std::vector<cudaStream_t> gstream;
   std::vector<cudaEvent_t> gdone;
   cudaEvent_t fork = nullptr;
+  // the step sequence of a call of nsteps steps, captured once as a CUDA graph
+  // and replayed on `cap` (a stream of the batch's own: the caller's stream may
+  // be the legacy default stream, which cannot be captured)
+  struct Graph {
+    int nsteps;
+    cudaGraphExec_t exec;
+    long long launches;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap = nullptr;
+  cudaEvent_t cap_in = nullptr, cap_out = nullptr;
+  size_t off_t0 = 0;  // device scalar: the call's start time
   char* ptr(size_t off) const { return static_cast<char*>(ws) + off; }
 };
 
@@ -249,6 +266,8 @@ fse_status fse_batch_create(const fse_params* runs, int nruns, void* stream, fse
       off = al(off + spec_bytes);
     }
   }
+  B->off_t0 = off;
+  off = al(off + sizeof(double));
   B->ws_bytes = off;
   *workspace_bytes = off;
   *out = B;
@@ -289,63 +308,34 @@ fse_status fse_batch_precompute(fse_batch_t B) {
   return FSE_OK;
 }
 
-fse_status fse_batch_step(fse_batch_t B, void* const* psi, double t0, int nsteps) {
-  if (!B || !psi || nsteps < 0) return FSE_ERR_INVALID;
-  if (!B->ws || !B->precomputed) return bfail(B, FSE_ERR_INVALID, "fse_batch_precompute has not run");
-  for (size_t r = 0; r < B->runs.size(); ++r)
-    if (!psi[r] || reinterpret_cast<uintptr_t>(psi[r]) % 8 != 0) return bfail(B, FSE_ERR_INVALID, "bad psi pointer");
-  if (nsteps == 0) return FSE_OK;
+}  // extern "C"
+
+namespace {
+
+// The launches of nsteps steps of every group, each group on its own stream
+// (forked from and joined back into `st`); the descriptor tables and the start
+// time are read from the workspace when the kernels run. Returns the number
+// of launches in *count.
+fse_status batch_sequence(fse_batch* B, int nsteps, cudaStream_t st0, long long* count) {
   const bool multi = B->groups.size() > 1;
-  if (multi && B->gstream.empty()) {
-    cudaError_t e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
-    for (size_t g = 0; g < B->groups.size() && e == cudaSuccess; ++g) {
-      cudaStream_t s = nullptr;
-      cudaEvent_t d = nullptr;
-      e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-      if (e == cudaSuccess) B->gstream.push_back(s);
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
-      if (e == cudaSuccess) B->gdone.push_back(d);
-    }
-    if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("group streams: ") + cudaGetErrorString(e));
-  }
+  long long nl = 0;
   if (multi) {
-    cudaError_t e = cudaEventRecord(B->fork, B->stream);
+    cudaError_t e = cudaEventRecord(B->fork, st0);
     for (size_t g = 0; g < B->groups.size() && e == cudaSuccess; ++g) e = cudaStreamWaitEvent(B->gstream[g], B->fork, 0);
     if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("group fork: ") + cudaGetErrorString(e));
   }
+  const double* t0 = reinterpret_cast<const double*>(B->ptr(B->off_t0));
   for (size_t gi = 0; gi < B->groups.size(); ++gi) {
     auto& G = B->groups[gi];
-    const cudaStream_t st = multi ? B->gstream[gi] : B->stream;
+    const cudaStream_t st = multi ? B->gstream[gi] : st0;
     fse_plan* P = G.plan;
     const int nr = (int)G.runs.size();
-    // descriptor table of the group
-    B->desc.resize(nr);
-    for (int k = 0; k < nr; ++k) {
-      const int r = G.runs[k];
-      const fse_params& p = B->runs[r];
-      BatchRun d;
-      d.psi = psi[r];
-      d.spec = k == 0 ? P->ws_ptr(P->off_spec) : B->ptr(B->off_spec[r]);
-      d.kin_half = k == 0 ? P->ws_ptr(P->off_kin_half) : B->ptr(B->off_kh[r]);
-      d.kin_full = k == 0 ? P->ws_ptr(P->off_kin_full) : B->ptr(B->off_kf[r]);
-      d.beta = p.beta;
-      d.lam = p.lambda;
-      d.dt = p.dt;
-      d.omega = p.omega;
-      d.gx2 = p.gamma[0] * p.gamma[0];
-      d.gy2 = p.gamma[1] * p.gamma[1];
-      B->desc[k] = d;
-    }
-    BatchRun* ddesc = reinterpret_cast<BatchRun*>(B->ptr(G.off_desc));
-    cudaError_t e = cudaMemcpyAsync(ddesc, B->desc.data(), sizeof(BatchRun) * nr, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("descriptor upload: ") + cudaGetErrorString(e));
-    const bool nl = B->runs[G.runs[0]].kernel != FSE_KERNEL_NONE;
-    XArgs xa = x_args(P, nullptr, nl ? reinterpret_cast<void*>(1) : nullptr);  // pointers come from the table
-    xa.use_spec = nl ? 1 : 0;
+    const BatchRun* ddesc = reinterpret_cast<const BatchRun*>(B->ptr(G.off_desc));
+    const bool nl_on = B->runs[G.runs[0]].kernel != FSE_KERNEL_NONE;
+    XArgs xa = x_args(P, nullptr, nl_on ? reinterpret_cast<void*>(1) : nullptr);  // pointers come from the table
+    xa.use_spec = nl_on ? 1 : 0;
     const void* twn = twiddle(P, P->nx);
     const void* tw2n = twiddle(P, 2 * P->nx);
-    const int ncx = xpass_ncol<float>(P->nx);
-    (void)ncx;
     MulArgs mk1;
     std::memset(&mk1, 0, sizeof(mk1));
     mk1.mode = MUL_KIN;
@@ -366,7 +356,7 @@ fse_status fse_batch_step(fse_batch_t B, void* const* psi, double t0, int nsteps
     ColArgs cg{nullptr, 0, P->sx, 1, P->nx + 1, P->ny, P->ny, tiles(P, 2 * P->ny, P->nx + 1)};
     auto chk = [&](cudaError_t ee, const char* w) -> fse_status {
       if (ee != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string(w) + ": " + cudaGetErrorString(ee));
-      ++B->launches;
+      ++nl;
       return FSE_OK;
     };
     fse_status s;
@@ -374,7 +364,7 @@ fse_status fse_batch_step(fse_batch_t B, void* const* psi, double t0, int nsteps
     for (int n = 0; n < nsteps; ++n) {
       if ((s = chk(launch_colb(P->ny, 1, ck, mk1, twiddle(P, P->ny), ddesc, nr, 0, n > 0, 0, st), "batch kinetic")) != FSE_OK)
         return s;
-      if (nl) {
+      if (nl_on) {
         if ((s = chk(launch_xb(XP_E, P->nx, xa, twn, tw2n, ddesc, nr, t0, n, st), "batch density")) != FSE_OK) return s;
         if ((s = chk(launch_colb(2 * P->ny, 2, cg, mk2, twiddle(P, 2 * P->ny), ddesc, nr, 1, 0, 0, st), "batch kernel")) != FSE_OK)
           return s;
@@ -388,19 +378,112 @@ fse_status fse_batch_step(fse_batch_t B, void* const* psi, double t0, int nsteps
     if ((s = chk(launch_xb(XP_INV, P->nx, xa, twn, tw2n, ddesc, nr, t0, nsteps, st), "batch x")) != FSE_OK) return s;
     if (multi) {
       cudaError_t e = cudaEventRecord(B->gdone[gi], st);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(B->stream, B->gdone[gi], 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st0, B->gdone[gi], 0);
       if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("group join: ") + cudaGetErrorString(e));
     }
   }
+  *count = nl;
+  return FSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fse_status fse_batch_step(fse_batch_t B, void* const* psi, double t0, int nsteps) {
+  if (!B || !psi || nsteps < 0) return FSE_ERR_INVALID;
+  if (!B->ws || !B->precomputed) return bfail(B, FSE_ERR_INVALID, "fse_batch_precompute has not run");
+  for (size_t r = 0; r < B->runs.size(); ++r)
+    if (!psi[r] || reinterpret_cast<uintptr_t>(psi[r]) % 8 != 0) return bfail(B, FSE_ERR_INVALID, "bad psi pointer");
+  if (nsteps == 0) return FSE_OK;
+  cudaError_t e = cudaSuccess;
+  if (B->gstream.empty()) {
+    // the batch's own streams (one per group, one to replay graphs on) and events
+    e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->cap_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->cap_out, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking);
+    for (size_t g = 0; g < B->groups.size() && e == cudaSuccess; ++g) {
+      cudaStream_t s = nullptr;
+      cudaEvent_t d = nullptr;
+      e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+      if (e == cudaSuccess) B->gstream.push_back(s);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&d, cudaEventDisableTiming);
+      if (e == cudaSuccess) B->gdone.push_back(d);
+    }
+    if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("batch streams: ") + cudaGetErrorString(e));
+  }
+  // this call's descriptor tables (wave-function pointers and run parameters)
+  // and start time, stream-ordered on the caller's stream ahead of the kernels
+  for (auto& G : B->groups) {
+    fse_plan* P = G.plan;
+    const int nr = (int)G.runs.size();
+    B->desc.resize(nr);
+    for (int k = 0; k < nr; ++k) {
+      const int r = G.runs[k];
+      const fse_params& p = B->runs[r];
+      BatchRun d;
+      d.psi = psi[r];
+      d.spec = k == 0 ? P->ws_ptr(P->off_spec) : B->ptr(B->off_spec[r]);
+      d.kin_half = k == 0 ? P->ws_ptr(P->off_kin_half) : B->ptr(B->off_kh[r]);
+      d.kin_full = k == 0 ? P->ws_ptr(P->off_kin_full) : B->ptr(B->off_kf[r]);
+      d.beta = p.beta;
+      d.lam = p.lambda;
+      d.dt = p.dt;
+      d.omega = p.omega;
+      d.gx2 = p.gamma[0] * p.gamma[0];
+      d.gy2 = p.gamma[1] * p.gamma[1];
+      B->desc[k] = d;
+    }
+    // pageable source: the copy is staged before the call returns
+    e = cudaMemcpyAsync(B->ptr(G.off_desc), B->desc.data(), sizeof(BatchRun) * nr, cudaMemcpyHostToDevice, B->stream);
+    if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("descriptor upload: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemcpyAsync(B->ptr(B->off_t0), &t0, sizeof(double), cudaMemcpyHostToDevice, B->stream);
+  if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("start time upload: ") + cudaGetErrorString(e));
+  // the captured step sequence for nsteps (captured at the first call with this count)
+  fse_batch::Graph* gr = nullptr;
+  for (auto& g : B->graphs)
+    if (g.nsteps == nsteps) gr = &g;
+  if (!gr) {
+    e = cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    long long nl = 0;
+    const fse_status sq = batch_sequence(B, nsteps, B->cap, &nl);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(B->cap, &graph);
+    if (sq != FSE_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return sq;
+    }
+    if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    B->graphs.push_back({nsteps, exec, nl});
+    gr = &B->graphs.back();
+  }
+  e = cudaEventRecord(B->cap_in, B->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(B->cap, B->cap_in, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(gr->exec, B->cap);
+  if (e == cudaSuccess) e = cudaEventRecord(B->cap_out, B->cap);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(B->stream, B->cap_out, 0);
+  if (e != cudaSuccess) return bfail(B, FSE_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+  B->launches += gr->launches;
   return FSE_OK;
 }
 
 fse_status fse_batch_destroy(fse_batch_t B) {
   if (!B) return FSE_OK;
+  for (auto& g : B->graphs) cudaGraphExecDestroy(g.exec);
   for (auto& G : B->groups) fse_plan_destroy(G.plan);
   for (cudaStream_t s : B->gstream) cudaStreamDestroy(s);
   for (cudaEvent_t e : B->gdone) cudaEventDestroy(e);
   if (B->fork) cudaEventDestroy(B->fork);
+  if (B->cap_in) cudaEventDestroy(B->cap_in);
+  if (B->cap_out) cudaEventDestroy(B->cap_out);
+  if (B->cap) cudaStreamDestroy(B->cap);
   delete B;
   return FSE_OK;
 }

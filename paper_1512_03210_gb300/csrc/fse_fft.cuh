@@ -398,12 +398,15 @@ __host__ __device__ constexpr int plan_lcm(int N) {
   return two * (three ? 3 : 1);
 }
 // elements per thread and threads per tile of NCOL lines of length N, CW columns per item
-__host__ __device__ constexpr int reg_elems(int N, int ncol, int cw = 1) {
+// (at most maxt threads per tile)
+__host__ __device__ constexpr int reg_elems(int N, int ncol, int cw = 1, int maxt = 512) {
   int e = plan_lcm(N) * cw;
-  while (N * ncol / e > 512) e *= 2;
+  while (N * ncol / e > maxt) e *= 2;
   return e;
 }
-__host__ __device__ constexpr int reg_threads(int N, int ncol, int cw = 1) { return N * ncol / reg_elems(N, ncol, cw); }
+__host__ __device__ constexpr int reg_threads(int N, int ncol, int cw = 1, int maxt = 512) {
+  return N * ncol / reg_elems(N, ncol, cw, maxt);
+}
 
 __device__ __forceinline__ void st_pair(float2* p, float2 a, float2 b) {
   *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);

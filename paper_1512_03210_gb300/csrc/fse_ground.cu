@@ -11,7 +11,9 @@
 // with L_z = -i (x d_y - y d_x) by spectral derivatives. The problem is posed
 // in the laboratory frame: V is the trap (harmonic plus optional lattice) and
 // the dipole axis is n. Every transform runs through the plan's FFT passes;
-// the BiCGStab vectors live in a caller-supplied workspace.
+// the BiCGStab vectors live in a caller-supplied workspace, and its scalars
+// (inner products, alpha, omega, beta, the residual) stay on the device: the
+// host reads them one iteration behind the GPU to stop the solve.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -197,6 +199,118 @@ __global__ void __launch_bounds__(256) k_gs_final(const double* part, int count,
   if (threadIdx.x == 0) out[blockIdx.x] = red[0];
 }
 
+// ---------------------------------------------------------------------------
+// BiCGStab scalars on the device. The state sc[] holds, in float64,
+//   rho (complex, sc[0..1]), rho_prev (sc[2..3]), alpha (sc[4..5]),
+//   omega (sc[6..7]), beta (sc[8..9]), ||b|| (sc[10]), ||r|| / ||b|| (sc[11]),
+//   done (sc[12]: converged or broken down), iterations (sc[13]), tol (sc[14]).
+// One-thread kernels update it from the inner products in out[] (written by
+// k_gs_final), and the vector updates read their coefficients from it, so an
+// inner iteration needs no host round trip. Once done is set, every update
+// leaves its output untouched.
+// ---------------------------------------------------------------------------
+enum { SC_RHO = 0, SC_RHOP = 2, SC_ALPHA = 4, SC_OM = 6, SC_BETA = 8, SC_BN = 10, SC_RES = 11, SC_DONE = 12,
+       SC_IT = 13, SC_TOL = 14, SC_SIZE = 16 };
+
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b) {
+  const double d = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 ld2(const double* p) { return make_double2(p[0], p[1]); }
+__device__ __forceinline__ void st2(double* p, double2 v) {
+  p[0] = v.x;
+  p[1] = v.y;
+}
+
+// after <s, s>, <r, r> (s = b, r = b - M x, rh = r): the start of an inner solve
+__global__ void k_gs_sc_init(double* sc, const double* out, double tol) {
+  const double bn = sqrt(out[0]);
+  const double res = bn > 0.0 ? sqrt(out[2]) / bn : 0.0;
+  st2(sc + SC_RHO, make_double2(out[2], out[3]));
+  st2(sc + SC_RHOP, make_double2(1.0, 0.0));
+  st2(sc + SC_ALPHA, make_double2(1.0, 0.0));
+  st2(sc + SC_OM, make_double2(1.0, 0.0));
+  st2(sc + SC_BETA, make_double2(0.0, 0.0));
+  sc[SC_BN] = bn;
+  sc[SC_RES] = res;
+  sc[SC_TOL] = tol;
+  sc[SC_IT] = 0.0;
+  sc[SC_DONE] = (!(res > tol) || (out[2] == 0.0 && out[3] == 0.0)) ? 1.0 : 0.0;
+}
+
+// after <rh, v>: alpha = rho / <rh, v> (breakdown when it vanishes)
+__global__ void k_gs_sc_alpha(double* sc, const double* out) {
+  if (sc[SC_DONE] != 0.0) return;
+  const double2 rv = make_double2(out[0], out[1]);
+  if (rv.x == 0.0 && rv.y == 0.0) {
+    sc[SC_DONE] = 1.0;
+    return;
+  }
+  st2(sc + SC_ALPHA, zdiv(ld2(sc + SC_RHO), rv));
+}
+
+// after <t, s>, <t, t>: omega = <t, s> / <t, t> (0 if <t, t> = 0)
+__global__ void k_gs_sc_omega(double* sc, const double* out) {
+  if (sc[SC_DONE] != 0.0) return;
+  st2(sc + SC_OM, out[2] > 0.0 ? make_double2(out[0] / out[2], out[1] / out[2]) : make_double2(0.0, 0.0));
+}
+
+// after <rh, r>, <r, r>: the end of an iteration
+__global__ void k_gs_sc_rho(double* sc, const double* out) {
+  if (sc[SC_DONE] != 0.0) return;
+  const double2 rho_prev = ld2(sc + SC_RHO), rho = make_double2(out[0], out[1]);
+  const double2 alpha = ld2(sc + SC_ALPHA), om = ld2(sc + SC_OM);
+  st2(sc + SC_RHOP, rho_prev);
+  st2(sc + SC_RHO, rho);
+  const double res = sqrt(out[2]) / sc[SC_BN];
+  sc[SC_RES] = res;
+  sc[SC_IT] += 1.0;
+  const bool om0 = om.x == 0.0 && om.y == 0.0, rho0 = rho.x == 0.0 && rho.y == 0.0;
+  if (om0 || rho0 || !(res > sc[SC_TOL])) {
+    sc[SC_DONE] = 1.0;
+    return;
+  }
+  // beta of the next iteration: (rho / rho_prev) (alpha / omega)
+  st2(sc + SC_BETA, zmul(zdiv(rho, rho_prev), zdiv(alpha, om)));
+}
+
+enum { GS_P = 0, GS_S = 1, GS_X = 2, GS_R = 3 };
+// The BiCGStab vector updates with coefficients from sc (nothing when done):
+//   GS_P: o = A + beta (o - omega Cc)   (o = A on the first iteration)
+//   GS_S: o = A - alpha Cc               GS_X: o = o + alpha A + omega Cc
+//   GS_R: o = A - omega Cc
+template <typename Real, int MODE>
+__global__ void k_gs_update(typename Cplx<Real>::T* o, const typename Cplx<Real>::T* A,
+                            const typename Cplx<Real>::T* Cc, const double* sc, long long N) {
+  typedef typename Cplx<Real>::T C;
+  if (sc[SC_DONE] != 0.0) return;
+  const double2 al = ld2(sc + SC_ALPHA), om = ld2(sc + SC_OM), be = ld2(sc + SC_BETA);
+  const bool first = sc[SC_IT] == 0.0;
+  C c1, c2;
+  if (MODE == GS_P) {
+    c1 = mk(Real(be.x), Real(be.y));
+    const double2 bo = zmul(be, om);
+    c2 = mk(Real(-bo.x), Real(-bo.y));
+  } else if (MODE == GS_S) {
+    c2 = mk(Real(-al.x), Real(-al.y));
+  } else if (MODE == GS_X) {
+    c1 = mk(Real(al.x), Real(al.y));
+    c2 = mk(Real(om.x), Real(om.y));
+  } else {
+    c2 = mk(Real(-om.x), Real(-om.y));
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N; i += (long long)gridDim.x * blockDim.x) {
+    C r;
+    if (MODE == GS_P) r = first ? A[i] : cadd(A[i], cadd(cmul(o[i], c1), cmul(Cc[i], c2)));
+    else if (MODE == GS_X) r = cadd(o[i], cadd(cmul(A[i], c1), cmul(Cc[i], c2)));
+    else r = cadd(A[i], cmul(Cc[i], c2));
+    o[i] = r;
+  }
+}
+
 // Spectral translation by x0 (the Nyquist mode takes cos(k_N x0), the mean of
 // its two aliases) and 1/N for the unnormalised inverse.
 template <typename Real>
@@ -282,7 +396,7 @@ size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 // workspace: 10 complex fields, 3 real fields, reduction partials and results
 struct GsLayout {
-  size_t cplx[10], real[3], part, out, total;
+  size_t cplx[10], real[3], part, out, sc, total;
 };
 GsLayout gs_layout(const fse_plan* P) {
   GsLayout L;
@@ -300,6 +414,8 @@ GsLayout gs_layout(const fse_plan* P) {
   off = al256(off + sizeof(double) * 4 * kGsBlocks);
   L.out = off;
   off = al256(off + sizeof(double) * 8);
+  L.sc = off;
+  off = al256(off + sizeof(double) * SC_SIZE);
   L.total = off;
   return L;
 }
@@ -314,7 +430,7 @@ struct Gs {
   GsGrid g;
   C *phin, *r, *rh, *p, *v, *s, *t, *t1, *t2, *t3;
   Real *W, *pk, *Phi;
-  double *part, *out;
+  double *part, *out, *sc;
   double omega;
 
   fse_status chk(const char* w) { return launched(P, cudaGetLastError(), w); }
@@ -344,6 +460,18 @@ struct Gs {
     d1 = std::complex<double>(h[0], h[1]);
     d2 = std::complex<double>(h[2], h[3]);
     return FSE_OK;
+  }
+  // the same two inner products into out[0..3], left on the device
+  fse_status dot2_dev(const C* a1, const C* b1, const C* a2, const C* b2) {
+    k_gs_dot2<Real><<<blocks, 256, 0, st>>>(a1, b1, a2, b2, N, part);
+    fse_status s0 = chk("ground state reduction");
+    if (s0 != FSE_OK) return s0;
+    k_gs_final<<<4, 256, 0, st>>>(part, blocks, 0, out);
+    return chk("ground state reduction");
+  }
+  template <int MODE> fse_status update(C* o, const C* A, const C* Cc) {
+    k_gs_update<Real, MODE><<<blocks, 256, 0, st>>>(o, A, Cc, sc, N);
+    return chk("ground state update");
   }
   fse_status maxdiff(const C* a, const C* b, double& m) {
     k_gs_maxdiff<Real><<<blocks, 256, 0, st>>>(a, b, N, part);
@@ -402,6 +530,7 @@ fse_status ground_state(fse_plan* P, void* psi_v, void* ws, const fse_gs_opts& o
   G.Phi = reinterpret_cast<Real*>(base + L.real[2]);
   G.part = reinterpret_cast<double*>(base + L.part);
   G.out = reinterpret_cast<double*>(base + L.out);
+  G.sc = reinterpret_cast<double*>(base + L.sc);
   G.omega = P->p.omega;
   C* x = static_cast<C*>(psi_v);
   const double hd = P->h[0] * P->h[1] * (P->dim == 3 ? P->h[2] : 1.0);
@@ -434,39 +563,49 @@ fse_status ground_state(fse_plan* P, void* psi_v, void* ws, const fse_gs_opts& o
     if ((st = G.matvec(x, G.v)) != FSE_OK) return st;
     if ((st = G.lincomb(G.r, G.s, 1.0, G.v, -1.0)) != FSE_OK) return st;
     if ((st = G.copy(G.rh, G.r)) != FSE_OK) return st;
-    std::complex<double> bb, rho, rr;
-    if ((st = G.dot2(G.s, G.s, G.r, G.r, bb, rr)) != FSE_OK) return st;
-    rho = rr;  // <rh, r> with rh = r
-    const double bn = std::sqrt(bb.real());
-    res = bn > 0.0 ? std::sqrt(rr.real()) / bn : 0.0;
-    std::complex<double> rho_prev = 1.0, alpha = 1.0, om = 1.0;
+    if ((st = G.dot2_dev(G.s, G.s, G.r, G.r)) != FSE_OK) return st;
+    k_gs_sc_init<<<1, 1, 0, G.st>>>(G.sc, G.out, o.inner_tol);
+    if ((st = G.chk("ground state scalars")) != FSE_OK) return st;
+    // Iterations are queued one ahead of the host: after queueing iteration
+    // it, the host waits for the scalars of iteration it - 1 (copied to pinned
+    // host memory behind it) and stops once they say done, so the GPU never
+    // idles on a read-back; the extra iteration then changes nothing.
+    double* hs = P->gs_host;
     int it = 0;
-    while (it < o.max_inner && res > o.inner_tol) {
-      if (std::abs(rho) == 0.0) break;
-      const std::complex<double> beta = (rho / rho_prev) * (alpha / om);
-      if (it == 0) {
-        if ((st = G.copy(G.p, G.r)) != FSE_OK) return st;
-      } else if ((st = G.lincomb(G.p, G.r, 1.0, G.p, beta, G.v, -beta * om)) != FSE_OK) {
-        return st;
-      }
+    for (; it < o.max_inner; ++it) {
+      if ((st = G.template update<GS_P>(G.p, G.r, G.v)) != FSE_OK) return st;
       if ((st = G.matvec(G.p, G.v)) != FSE_OK) return st;
-      std::complex<double> rv, d2;
-      if ((st = G.dot2(G.rh, G.v, G.rh, G.v, rv, d2)) != FSE_OK) return st;
-      if (std::abs(rv) == 0.0) break;
-      alpha = rho / rv;
-      if ((st = G.lincomb(G.s, G.r, 1.0, G.v, -alpha)) != FSE_OK) return st;
+      if ((st = G.dot2_dev(G.rh, G.v, G.rh, G.v)) != FSE_OK) return st;
+      k_gs_sc_alpha<<<1, 1, 0, G.st>>>(G.sc, G.out);
+      if ((st = G.chk("ground state scalars")) != FSE_OK) return st;
+      if ((st = G.template update<GS_S>(G.s, G.r, G.v)) != FSE_OK) return st;
       if ((st = G.matvec(G.s, G.t)) != FSE_OK) return st;
-      std::complex<double> ts, tt;
-      if ((st = G.dot2(G.t, G.s, G.t, G.t, ts, tt)) != FSE_OK) return st;
-      om = tt.real() > 0.0 ? ts / tt.real() : std::complex<double>(0.0);
-      if ((st = G.lincomb(x, x, 1.0, G.p, alpha, G.s, om)) != FSE_OK) return st;
-      if ((st = G.lincomb(G.r, G.s, 1.0, G.t, -om)) != FSE_OK) return st;
-      rho_prev = rho;
-      if ((st = G.dot2(G.rh, G.r, G.r, G.r, rho, rr)) != FSE_OK) return st;
-      res = std::sqrt(rr.real()) / bn;
-      ++it;
-      if (std::abs(om) == 0.0) break;
+      if ((st = G.dot2_dev(G.t, G.s, G.t, G.t)) != FSE_OK) return st;
+      k_gs_sc_omega<<<1, 1, 0, G.st>>>(G.sc, G.out);
+      if ((st = G.chk("ground state scalars")) != FSE_OK) return st;
+      if ((st = G.template update<GS_X>(x, G.p, G.s)) != FSE_OK) return st;
+      if ((st = G.template update<GS_R>(G.r, G.s, G.t)) != FSE_OK) return st;
+      if ((st = G.dot2_dev(G.rh, G.r, G.r, G.r)) != FSE_OK) return st;
+      k_gs_sc_rho<<<1, 1, 0, G.st>>>(G.sc, G.out);
+      if ((st = G.chk("ground state scalars")) != FSE_OK) return st;
+      cudaError_t e = cudaMemcpyAsync(hs + (it & 1) * SC_SIZE, G.sc, sizeof(double) * SC_SIZE,
+                                      cudaMemcpyDeviceToHost, G.st);
+      if (e == cudaSuccess) e = cudaEventRecord(P->gs_ev[it & 1], G.st);
+      if (e != cudaSuccess) return cuda_fail(P, e, "ground state scalars");
+      if (it >= 1) {
+        if ((e = cudaEventSynchronize(P->gs_ev[(it - 1) & 1])) != cudaSuccess)
+          return cuda_fail(P, e, "ground state scalars");
+        if (hs[((it - 1) & 1) * SC_SIZE + SC_DONE] != 0.0) break;
+      }
     }
+    // the scalars after the last queued iteration (iteration count, residual)
+    {
+      cudaError_t e = cudaMemcpyAsync(hs, G.sc, sizeof(double) * SC_SIZE, cudaMemcpyDeviceToHost, G.st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(G.st);
+      if (e != cudaSuccess) return cuda_fail(P, e, "ground state scalars");
+    }
+    it = (int)hs[SC_IT];
+    res = hs[SC_RES];
     inner += it;
     // phi^{n+1} = phi^(1) / ||phi^(1)||
     if ((st = G.dot2(x, x, x, x, m2, dummy)) != FSE_OK) return st;
@@ -508,6 +647,17 @@ extern "C" fse_status fse_ground_state(fse_plan_t P, void* psi, void* workspace,
   if (!(opts->dt > 0.0) || opts->max_outer < 0 || opts->max_inner < 0 || !(opts->tol >= 0.0) ||
       !(opts->inner_tol >= 0.0))
     return fail(P, FSE_ERR_INVALID, "ground state: bad options");
+  if (!P->gs_host) {
+    void* h = nullptr;
+    cudaError_t e = cudaMallocHost(&h, sizeof(double) * 2 * SC_SIZE);
+    if (e != cudaSuccess) return cuda_fail(P, e, "ground state host scalars");
+    P->gs_host = static_cast<double*>(h);
+  }
+  for (auto& ev : P->gs_ev) {
+    if (ev) continue;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(P, e, "ground state events");
+  }
   return P->prec == FSE_F32 ? ground_state<float>(P, psi, workspace, *opts, info)
                             : ground_state<double>(P, psi, workspace, *opts, info);
 }

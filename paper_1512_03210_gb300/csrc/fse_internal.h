@@ -39,6 +39,12 @@ struct fse_plan {
   struct Rec { int kind; cudaEvent_t a, b; };
   std::vector<Rec> recs;
 
+  // ground state: page-locked copies of the device-side Krylov scalars (two
+  // slots of 16 doubles) and the events that order their reads (created at
+  // the first fse_ground_state call, released by fse_plan_destroy)
+  double* gs_host = nullptr;
+  cudaEvent_t gs_ev[2] = {nullptr, nullptr};
+
   void* ws = nullptr;
   bool precomputed = false;
   long long launches = 0;

@@ -20,6 +20,7 @@
 #pragma once
 
 #include "fse_fft.cuh"
+#include "fse_fft_x2.cuh"
 
 namespace fse {
 
@@ -200,9 +201,18 @@ struct ColCfg {
   // columns (16-byte row accesses, shared twiddles); otherwise one column
   static constexpr int CW = (sizeof(C) == 8 && plan_lcm(N) <= 8 && NCOL % 2 == 0) ? 2 : 1;
   static constexpr int NCP = NCOL / CW;
-  static constexpr int LDS = CW == 2 ? NCOL + 2 : NCOL + 1;  // even for 16-byte pairs
-  static constexpr int E = reg_elems(N, NCOL, CW);
-  static constexpr int NT = reg_threads(N, NCOL, CW);
+  // leading dimension of the exchange tile: a column pair is one 16-byte slot
+  // and the 8 threads of a quarter warp always touch the NCOL / 2 slots of one
+  // row, so pairs need no padding; single columns pad to NCOL + 1
+  static constexpr int LDS = CW == 2 ? NCOL : NCOL + 1;
+#ifndef FSE_X2_MAXT
+#define FSE_X2_MAXT 256
+#endif
+  // packed pairs (CW = 2): at most FSE_X2_MAXT threads per tile, so that a
+  // long transform keeps two items per thread and the registers for them
+  static constexpr int MAXT = CW == 2 ? FSE_X2_MAXT : 512;
+  static constexpr int E = reg_elems(N, NCOL, CW, MAXT);
+  static constexpr int NT = reg_threads(N, NCOL, CW, MAXT);
   static constexpr int R0 = radix_plan(N).r[0];
   static constexpr int RL = radix_plan(N).r[radix_plan(N).npass - 1];
   static constexpr int MINB = (sizeof(C) == 8 && E > 16) ? (512 / NT > 0 ? 512 / NT : 1) : minb_for(NT, sizeof(C));
@@ -212,6 +222,11 @@ struct ColCfg {
   __host__ __device__ static constexpr size_t chat_bytes() { return sizeof(Real) * (size_t)(N / 2 + 1) * NCOL; }
   __host__ __device__ static constexpr size_t base_bytes(int var) { return tile_bytes() + (var == 5 ? chat_bytes() : 0); }
   __host__ __device__ static constexpr size_t smem_bytes(int var) { return base_bytes(var); }
+  // pairs: first-pass inputs per thread (rows of the zero half of a padded
+  // line are not read)
+  __host__ __device__ static constexpr bool half_in(int var) { return var == 2 || var == 5; }
+  __host__ __device__ static constexpr int rh(int var) { return half_in(var) ? R0 / 2 : R0; }
+  __host__ __device__ static constexpr int first(int var) { return (E / 2 / R0) * rh(var); }
 };
 
 // One tile of a column pass: NCOL adjacent columns of one plane, or (GATHER)
@@ -476,15 +491,293 @@ __device__ __forceinline__ void colpass_tile(const ColArgs& a, const MulArgs& m,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Float column passes on pairs of adjacent columns (ColCfg::CW == 2) with
+// packed two-lane arithmetic (fse_fft_x2.cuh): the same passes, zero halves,
+// crops and multipliers as colpass_tile, each scalar operation of one column
+// done for both columns of a pair in one instruction. A tile is its geometry
+// (X2Geo), the first pass's row loads and the transform itself (x2_compute).
+// ---------------------------------------------------------------------------
+
+// This thread's column pair of one tile.
+struct X2Geo {
+  int plane, c0;
+  int my_plane[2], my_px[2];
+  bool my_ok[2];
+  float2* colp[2];
+  bool vec;  // both columns valid, adjacent and 16-byte aligned: one access per row
+};
+
+template <int N, int VAR, bool GATHER>
+__device__ __forceinline__ void x2_geo(const ColArgs& a, const MulArgs& m, int bid, int ngat, X2Geo& g, int tid) {
+  typedef ColCfg<float, N> K;
+  constexpr int NCOL = K::NCOL, NCP = K::NCP;
+  const int cg = tid % NCP;  // this thread's columns of the tile: 2 cg, 2 cg + 1
+  const int breg = bid - ngat;
+  const int tp = GATHER ? 0 : breg / a.tiles_per_plane;
+  g.c0 = GATHER ? 0 : (breg - tp * a.tiles_per_plane) * NCOL;
+  // kernel-transform pass over a full even set of planes: planes p and lp - p
+  // (same |p|, same C^ values) run next to each other, so the octant is read
+  // from HBM about once
+  g.plane = (VAR == COL_KHAT && m.lp == a.nplanes && (m.lp & 1) == 0 && tp > 0)
+                ? ((tp & 1) ? (tp + 1) >> 1 : m.lp - (tp >> 1))
+                : tp;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int cc = cg * 2 + q;
+    if (!GATHER) {
+      g.my_plane[q] = g.plane;
+      g.my_px[q] = g.c0 + cc;
+      g.my_ok[q] = g.my_px[q] < a.ncols;
+    } else {
+      const int qq = bid * NCOL + cc;
+      g.my_plane[q] = qq / a.tail;
+      g.my_px[q] = a.tiles_per_plane * NCOL + qq % a.tail;
+      g.my_ok[q] = g.my_plane[q] < a.nplanes;
+      if (!g.my_ok[q]) g.my_plane[q] = g.my_px[q] = 0;
+    }
+    g.colp[q] = (!GATHER && q > 0) ? g.colp[0] + q
+                                   : reinterpret_cast<float2*>(a.data) + (long long)g.my_plane[q] * a.plane_stride +
+                                         g.my_px[q];
+  }
+  g.vec = !GATHER && g.my_ok[0] && g.my_ok[1] && (reinterpret_cast<uintptr_t>(g.colp[0]) % 16 == 0) &&
+          (a.line_stride % 2 == 0);
+}
+
+__device__ __forceinline__ P2 x2_load_row(const ColArgs& a, const X2Geo& g, int row) {
+  if (row >= a.n_load) return P2{bc(0.f), bc(0.f)};
+  if (g.vec) return p2_from_row(*reinterpret_cast<const float4*>(&g.colp[0][(long long)row * a.line_stride]));
+  const float2 z = make_float2(0.f, 0.f);
+  const float2 u0 = g.my_ok[0] ? g.colp[0][(long long)row * a.line_stride] : z;
+  const float2 u1 = g.my_ok[1] ? g.colp[1][(long long)row * a.line_stride] : z;
+  return P2{make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
+}
+
+__device__ __forceinline__ void x2_store_row(const ColArgs& a, const X2Geo& g, int row, const P2& v) {
+  if (g.vec) {
+    *reinterpret_cast<float4*>(&g.colp[0][(long long)row * a.line_stride]) = p2_to_row(v);
+  } else {
+    if (g.my_ok[0]) g.colp[0][(long long)row * a.line_stride] = make_float2(v.re.x, v.im.x);
+    if (g.my_ok[1]) g.colp[1][(long long)row * a.line_stride] = make_float2(v.re.y, v.im.y);
+  }
+}
+
+// Row of the first-pass input c of this thread (items i, radix index r; the
+// zero half of a padded line is never read), c < ColCfg::first(VAR).
+template <int N, int VAR> __device__ __forceinline__ int x2_first_row(int c, int tid) {
+  typedef ColCfg<float, N> K;
+  constexpr int RH = K::rh(VAR);
+  const int i = c / RH, r = c % RH;
+  return (tid + i * K::NT) / K::NCP + r * (N / K::R0);
+}
+
+// The first pass's inputs into registers, straight from global memory.
+template <int N, int VAR>
+__device__ __forceinline__ void x2_first_loads(const ColArgs& a, const X2Geo& g, P2 (&v)[ColCfg<float, N>::E / 2],
+                                               int tid) {
+  typedef ColCfg<float, N> K;
+  constexpr int RH = K::rh(VAR), R0 = K::R0;
+#pragma unroll
+  for (int c = 0; c < K::first(VAR); ++c) {
+    const int i = c / RH, r = c % RH;
+    v[i * R0 + r] = x2_load_row(a, g, x2_first_row<N, VAR>(c, tid));
+  }
+}
+
+// Starts the cp.async copies of the tile's C^ values (|p_row| = 0..N/2) into
+// shared memory (the caller commits the group).
+template <int N, int VAR, bool GATHER>
+__device__ __forceinline__ void x2_chat_issue(const ColArgs& a, const MulArgs& m, const X2Geo& g, int bid,
+                                              float* sC, int tid) {
+  typedef ColCfg<float, N> K;
+  constexpr int NCOL = K::NCOL, NT = K::NT;
+  const float* ch = reinterpret_cast<const float*>(m.chat);
+  if (!GATHER) {
+    // the tile's columns of a C^ row are contiguous and 16-byte aligned (rows
+    // padded to a multiple of 4 values, c0 a multiple of NCOL): one 16-byte
+    // copy per 4 values; copies past the padded row are zero-filled
+    constexpr int CPR = NCOL / 4;
+    const float* chp = ch + (m.lp ? (long long)abs(wrap_index(g.plane, m.lp)) * m.chat_sp : 0) + g.c0;
+    const int left = m.chat_cx - g.c0;
+    for (int idx = tid; idx < (N / 2 + 1) * CPR; idx += NT) {
+      const int ar = idx / CPR, qd = idx - ar * CPR;
+      float* dst = &sC[ar * NCOL + qd * 4];
+      if (qd * 4 < left) cp_async<16>(dst, &chp[(long long)ar * m.chat_sr + qd * 4]);
+      else *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  } else {
+    for (int idx = tid; idx < (N / 2 + 1) * NCOL; idx += NT) {
+      const int ar = idx / NCOL, cc = idx % NCOL;
+      const int qq = bid * NCOL + cc;
+      const int pl = qq / a.tail, px = a.tiles_per_plane * NCOL + qq % a.tail;
+      const int ap = m.lp ? abs(wrap_index(pl, m.lp)) : 0;
+      if (pl < a.nplanes && px <= (m.lx >> 1))
+        cp_async<4>(&sC[idx], &ch[(long long)ar * m.chat_sr + (long long)ap * m.chat_sp + px]);
+      else
+        sC[idx] = 0.f;
+    }
+  }
+}
+
+// Transform, multiplier, inverse transform and stores of one tile whose
+// first-pass inputs are in v. For the kernel-transform variant the tile's C^
+// copies are the second most recent cp.async group of this thread.
+template <int N, int VAR>
+__device__ __forceinline__ void x2_compute(const ColArgs& a, const MulArgs& m, const float2* __restrict__ tw,
+                                           const X2Geo& g, P2 (&v)[ColCfg<float, N>::E / 2], int tid) {
+  typedef ColCfg<float, N> K;
+  constexpr int NCOL = K::NCOL, NCP = K::NCP, LDS = K::LDS, NT = K::NT, W = K::E / 2;
+  constexpr int R0 = K::R0, RL = K::RL;
+  constexpr bool FUSED = (VAR == COL_KIN || VAR == COL_KHAT) && plan_palindrome(N);
+  constexpr int RF = FUSED ? R0 : RL;
+  constexpr bool HALF_IN = (VAR == COL_PADF || VAR == COL_KHAT);
+  constexpr bool HALF_OUT = (VAR == COL_CROPI || VAR == COL_KHAT);
+  constexpr bool EXACT = (VAR == COL_FWD || VAR == COL_INV || VAR == COL_KIN);
+  constexpr int DIR1 = (VAR == COL_INV || VAR == COL_CROPI) ? +1 : -1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* buf = reinterpret_cast<float2*>(smem_raw);
+  const float* sC = reinterpret_cast<const float*>(smem_raw + K::TILE_BYTES);
+  const float4* twb = twb_of<N>(tw);
+  const int cg = tid % NCP;
+  if constexpr (VAR == COL_FWD || VAR == COL_INV || VAR == COL_PADF || VAR == COL_CROPI) {
+    pregs_fft<N, NCP, NT, W, LDS, DIR1, EXACT, 0, 1, false, HALF_IN>(v, buf, twb, tid);
+  } else {
+    pregs_fft<N, NCP, NT, W, LDS, -1, EXACT, 0, 1, false, HALF_IN>(v, buf, twb, tid);
+    if constexpr (VAR == COL_KIN) {
+      // kinetic phase exp(-i f theta_k) of both columns from the octant table,
+      // its modulus error folded into the products (unit_mul), times 1/N
+      const float2* tab[2];
+      int ax[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        tab[q] = reinterpret_cast<const float2*>(m.kin) +
+                 (m.lp ? (long long)abs(wrap_index(g.my_plane[q], m.lp)) * m.kin_sp : 0);
+        ax[q] = abs(wrap_index(min(g.my_px[q], m.lx - 1), m.lx));
+      }
+      const float2 sc = bc(m.f.scale);
+      const bool conj = m.conj != 0;
+#pragma unroll
+      for (int i = 0; i < W / RL; ++i) {
+        const int j = (tid + i * NT) / NCP;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int row = j + r * (N / RL);
+          const long long ro = (long long)abs(wrap_index(row, m.lr)) * m.kin_sr;
+          const float2 t0 = g.my_ok[0] ? __ldg(&tab[0][ro + ax[0]]) : make_float2(1.f, 0.f);
+          const float2 t1 = g.my_ok[1] ? __ldg(&tab[1][ro + ax[1]]) : make_float2(1.f, 0.f);
+          // factor c + i s (conjugated for the adjoint) with its modulus remainder h (c + i s)
+          const float2 c2 = make_float2(t0.x, t1.x);
+          const float2 s2 = conj ? make_float2(-t0.y, -t1.y) : make_float2(t0.y, t1.y);
+          const float2 h2 = make_float2(-0.5f * norm_err(t0.x, t0.y), -0.5f * norm_err(t1.x, t1.y));
+          const float2 lc = mul2(h2, c2), ls = mul2(h2, s2);
+          const P2 x = v[i * RL + r];
+          const float2 lr = fma2(x.re, lc, mul2(x.im, neg2(ls)));
+          const float2 li = fma2(x.re, ls, mul2(x.im, lc));
+          const float2 yr = fma2(x.re, c2, fma2(x.im, neg2(s2), lr));
+          const float2 yi = fma2(x.re, s2, fma2(x.im, c2, li));
+          const P2 y{mul2(sc, yr), mul2(sc, yi)};
+          if constexpr (FUSED) v[i * RL + r] = y;
+          else p2_st(&buf[row * LDS + 2 * cg], y);
+        }
+      }
+    } else {
+      // kernel transform on the padded grid: f = a0 C^ (Coulomb) or a0 + (k^T Q k) C^ (DDI);
+      // the column (x, an R2C bin 0..nx) and plane factors are fixed per thread
+      cp_async_wait_group<1>();
+      __syncthreads();
+      const bool ddi = m.mode == MUL_DDI;
+      float Aq[2], Bq[2];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const float kp = m.lp ? m.f.dkp * float(wrap_index(g.my_plane[q], m.lp)) : 0.f;
+        const float kpo = (m.lp && 2 * g.my_plane[q] == m.lp) ? 0.f : kp;
+        const float kx = m.f.dkx * float(g.my_px[q]);
+        const float kxo = (2 * g.my_px[q] == m.lx) ? 0.f : kx;
+        Aq[q] = m.f.q[0] * kx * kx + m.f.q[1] * kp * kp + m.f.q[3] * kxo * kpo;
+        Bq[q] = m.f.q[4] * kxo + m.f.q[5] * kpo;
+      }
+      const float2 A2 = make_float2(Aq[0], Aq[1]), B2 = make_float2(Bq[0], Bq[1]);
+      const float2 a02 = bc(m.f.a0);
+#pragma unroll
+      for (int i = 0; i < W / RL; ++i) {
+        const int j = (tid + i * NT) / NCP;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+          const int row = j + r * (N / RL);
+          const int pr = wrap_index(row, m.lr);
+          const float kr = m.f.dkr * float(pr);
+          const float kro = (2 * row == m.lr) ? 0.f : kr;
+          const float2 cv = *reinterpret_cast<const float2*>(&sC[abs(pr) * NCOL + 2 * cg]);
+          // f = a0 + q(k) C^ with q(k) = A + B kr + q2 kr^2 (DDI), or a0 C^
+          const float2 f = ddi ? fma2(fma2(B2, bc(kro), add2(A2, bc(m.f.q[2] * kr * kr))), cv, a02) : mul2(a02, cv);
+          const P2 x = v[i * RL + r];
+          const P2 y{mul2(f, x.re), mul2(f, x.im)};
+          if constexpr (FUSED) v[i * RL + r] = y;
+          else p2_st(&buf[row * LDS + 2 * cg], y);
+        }
+      }
+    }
+    if constexpr (!FUSED) {
+      __syncthreads();
+      psmem_to_regs<N, NCP, NT, W, R0, LDS>(v, buf, tid);
+      __syncthreads();
+    }
+    pregs_fft<N, NCP, NT, W, LDS, +1, EXACT, 0, 1, FUSED>(v, buf, twb, tid);
+  }
+  // outputs of the last pass to global memory (rows >= n_store cropped)
+#pragma unroll
+  for (int i = 0; i < W / RF; ++i) {
+    const int j = (tid + i * NT) / NCP;
+#pragma unroll
+    for (int r = 0; r < RF; ++r) {
+      const int row = j + r * (N / RF);
+      if (HALF_OUT && 2 * r >= RF) continue;  // rows >= N/2 are cropped
+      if (row >= a.n_store) continue;
+      x2_store_row(a, g, row, v[i * RF + r]);
+    }
+  }
+}
+
+// One tile (block bid).
+template <int N, int VAR, bool GATHER>
+__device__ __forceinline__ void colpass_tile_x2(const ColArgs& a, const MulArgs& m, const float2* __restrict__ tw,
+                                                int bid, int ngat) {
+  typedef ColCfg<float, N> K;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int tid = threadIdx.x;
+  X2Geo g;
+  x2_geo<N, VAR, GATHER>(a, m, bid, ngat, g, tid);
+  if constexpr (VAR == COL_KHAT) {
+    x2_chat_issue<N, VAR, GATHER>(a, m, g, bid, reinterpret_cast<float*>(smem_raw + K::TILE_BYTES), tid);
+    cp_async_commit();
+  }
+  cp_async_commit();  // an empty group: the C^ copies are the second most recent
+  P2 v[K::E / 2];
+  x2_first_loads<N, VAR>(a, g, v, tid);
+  x2_compute<N, VAR>(a, m, tw, g, v, tid);
+}
+
+// Persistent column pass (float pairs): block b transforms tiles b, b + G,
+// b + 2G, ... (G = gridDim.x, the blocks resident on the device). While a tile
+// is transformed, each thread's cp.async copies bring the first-pass rows of
+// its column pair of the next tile into its own staging slots, so no barrier
+// guards the staging area: a thread only ever reads the slots it filled. The
+// gathered tail tiles come first and load directly.
 template <typename Real, int N, int VAR>
 __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
                                              const typename Cplx<Real>::T* __restrict__ tw, int bid) {
   // only passes over R2C bins (ncols = nx + 1) have tail tiles; they come
   // first in the grid, so that they overlap the full tiles
   constexpr bool TAILS = (VAR == COL_PADF || VAR == COL_CROPI || VAR == COL_KHAT);
-  if constexpr (TAILS) {
-    constexpr int NCOL = ColCfg<Real, N>::NCOL;
-    const int ngat = a.tail > 0 ? (a.nplanes * a.tail + NCOL - 1) / NCOL : 0;
+  constexpr bool X2 = ColCfg<Real, N>::CW == 2;  // float pairs: packed arithmetic
+  constexpr int NCOL = ColCfg<Real, N>::NCOL;
+  const int ngat = (TAILS && a.tail > 0) ? (a.nplanes * a.tail + NCOL - 1) / NCOL : 0;
+  if constexpr (X2 && TAILS) {
+    if (bid < ngat) colpass_tile_x2<N, VAR, true>(a, m, tw, bid, ngat);
+    else colpass_tile_x2<N, VAR, false>(a, m, tw, bid, ngat);
+  } else if constexpr (X2) {
+    colpass_tile_x2<N, VAR, false>(a, m, tw, bid, 0);
+  } else if constexpr (TAILS) {
     if (bid < ngat) colpass_tile<Real, N, VAR, true>(a, m, tw, bid, ngat);
     else colpass_tile<Real, N, VAR, false>(a, m, tw, bid, ngat);
   } else {

@@ -36,6 +36,8 @@ __device__ __forceinline__ void round_pair(double c, double s, float2* out) {
 }
 __device__ __forceinline__ void round_pair(double c, double s, double2* out) { *out = make_double2(c, s); }
 
+// For float tables the broadcast copy for the packed column passes follows at
+// tw + 2L: twb[2m] = (c, c, s, s) of tw[2m] and twb[2m+1] the same of tw[2m+1].
 template <typename Real>
 __global__ void k_twiddles(typename Cplx<Real>::T* tw, int L) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
@@ -45,6 +47,12 @@ __global__ void k_twiddles(typename Cplx<Real>::T* tw, int L) {
   round_pair(c, s, &tw[2 * m]);
   // rounded remainder of the exact twiddle (second term of the exact products)
   tw[2 * m + 1] = mk(Real(c - (double)tw[2 * m].x), Real(s - (double)tw[2 * m].y));
+  if constexpr (sizeof(Real) == 4) {
+    float4* twb = reinterpret_cast<float4*>(tw + 2 * L);
+    const float2 w = tw[2 * m], l = tw[2 * m + 1];
+    twb[2 * m] = make_float4(w.x, w.x, w.y, w.y);
+    twb[2 * m + 1] = make_float4(l.x, l.x, l.y, l.y);
+  }
 }
 
 // Kinetic multipliers exp(-i theta_k) (half step, theta = dt/4 (|k|^2+m^2)^s)

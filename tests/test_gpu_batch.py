@@ -106,3 +106,28 @@ def test_batch_workload_sizes_match_oracle(lib):
         plan.step(y, 0.0, 3)
         torch.cuda.synchronize()
         assert torch.equal(x, y)
+
+
+def test_batch_graph_replay_matches_single_runs(lib):
+    """Two calls with the same step count (the second one replays the graph the
+    first one captured, with new wave-function pointers and a new start time)
+    and a call with another count: each run bit-identical to the same calls of
+    fse_step on a plan of its own."""
+    runs = _runs()
+    psis = [_psi(d, 30 + k) for k, d in enumerate(runs)]
+    b = lib.Batch(runs)
+    xs = b.to_device(psis)
+    dt = runs[0]["dt"]
+    b.step(xs, 0.1, 3)
+    ys = [x.clone() for x in xs]   # fresh buffers for the replay
+    b.step(ys, 0.1 + 3 * dt, 3)
+    b.step(ys, 0.1 + 6 * dt, 2)
+    torch.cuda.synchronize()
+    for d, p0, y in zip(runs, psis, ys):
+        plan = lib.Plan(d)
+        z = plan.to_device(p0)
+        plan.step(z, 0.1, 3)
+        plan.step(z, 0.1 + 3 * dt, 3)
+        plan.step(z, 0.1 + 6 * dt, 2)
+        torch.cuda.synchronize()
+        assert torch.equal(y, z)
