@@ -278,12 +278,15 @@ typedef struct {
  * its Krylov vectors on this plan: ten complex and three real fields. */
 fse_status fse_ground_state_workspace(fse_plan_t plan, size_t* bytes);
 /* psi (device, plan layout): initial guess on entry (scaled to unit mass),
- * the last iterate on return. The BiCGStab scalars stay on the device; the
- * host reads them one iteration behind the GPU (so one extra, idempotent
- * iteration may run after convergence) and the call returns with the plan's
- * stream synchronised. It uses the plan's scratch field and spectrum, and
- * keeps 256 bytes of page-locked host memory and two events on the plan
- * (released by fse_plan_destroy). info (nullable) receives the counts. Errors: FSE_ERR_INVALID (null
+ * the last iterate on return. The BiCGStab scalars stay on the device, so
+ * the launches of one iteration are captured once per call as a CUDA graph
+ * and replayed; the host reads the scalars one iteration behind the GPU (one
+ * extra, idempotent iteration may run after convergence). The solve runs on
+ * a stream the plan creates at the first call, ordered after and before the
+ * plan's stream, and the call returns with the plan's stream synchronised. It
+ * uses the plan's scratch field and spectrum, and keeps that stream, four
+ * events and 256 bytes of page-locked host memory on the plan (released by
+ * fse_plan_destroy). info (nullable) receives the counts. Errors: FSE_ERR_INVALID (null
  * or misaligned buffers, precompute not run, dt <= 0, negative counts or
  * tolerances, zero initial field), FSE_ERR_NOMEM (workspace too small),
  * FSE_ERR_NONFINITE (the iteration produced a non-finite field). */

@@ -788,6 +788,9 @@ fse_status fse_plan_destroy(fse_plan_t P) {
   for (auto e : P->gs_ev)
     if (e) cudaEventDestroy(e);
   if (P->gs_host) cudaFreeHost(P->gs_host);
+  if (P->gs_fork) cudaEventDestroy(P->gs_fork);
+  if (P->gs_join) cudaEventDestroy(P->gs_join);
+  if (P->gs_stream) cudaStreamDestroy(P->gs_stream);
   delete P;
   return FSE_OK;
 }

@@ -548,6 +548,55 @@ fse_status ground_state(fse_plan* P, void* psi_v, void* ws, const fse_gs_opts& o
   const double3 g2 = make_double3(0.5 * P->p.gamma[0] * P->p.gamma[0], 0.5 * P->p.gamma[1] * P->p.gamma[1],
                                   P->dim == 3 ? 0.5 * P->p.gamma[2] * P->p.gamma[2] : 0.0);
   const double3 lk = make_double3(P->p.lat_k[0], P->p.lat_k[1], P->dim == 3 ? P->p.lat_k[2] : 0.0);
+  // one BiCGStab iteration: every operand and coefficient is on the device, so
+  // the launches are captured once per call as a CUDA graph and replayed
+  auto iteration = [&]() -> fse_status {
+    fse_status s0;
+    if ((s0 = G.template update<GS_P>(G.p, G.r, G.v)) != FSE_OK) return s0;
+    if ((s0 = G.matvec(G.p, G.v)) != FSE_OK) return s0;
+    if ((s0 = G.dot2_dev(G.rh, G.v, G.rh, G.v)) != FSE_OK) return s0;
+    k_gs_sc_alpha<<<1, 1, 0, G.st>>>(G.sc, G.out);
+    if ((s0 = G.chk("ground state scalars")) != FSE_OK) return s0;
+    if ((s0 = G.template update<GS_S>(G.s, G.r, G.v)) != FSE_OK) return s0;
+    if ((s0 = G.matvec(G.s, G.t)) != FSE_OK) return s0;
+    if ((s0 = G.dot2_dev(G.t, G.s, G.t, G.t)) != FSE_OK) return s0;
+    k_gs_sc_omega<<<1, 1, 0, G.st>>>(G.sc, G.out);
+    if ((s0 = G.chk("ground state scalars")) != FSE_OK) return s0;
+    if ((s0 = G.template update<GS_X>(x, G.p, G.s)) != FSE_OK) return s0;
+    if ((s0 = G.template update<GS_R>(G.r, G.s, G.t)) != FSE_OK) return s0;
+    if ((s0 = G.dot2_dev(G.rh, G.r, G.r, G.r)) != FSE_OK) return s0;
+    k_gs_sc_rho<<<1, 1, 0, G.st>>>(G.sc, G.out);
+    return G.chk("ground state scalars");
+  };
+  cudaGraphExec_t iter_exec = nullptr;
+  long long iter_launches = 0;
+  if (o.max_inner > 0 && o.max_outer > 0) {
+    // capture on the solve's own stream; if capture is refused (e.g. the
+    // thread is capturing another stream) the iterations are launched directly
+    const long long l0 = P->launches;
+    if (cudaStreamBeginCapture(G.st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const fse_status sq = iteration();
+      cudaGraph_t graph = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(G.st, &graph);
+      if (sq != FSE_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return sq != FSE_OK ? sq : cuda_fail(P, e, "ground state capture");
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&iter_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) return cuda_fail(P, ei, "ground state capture");
+      iter_launches = P->launches - l0;
+      P->launches = l0;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  struct ExecGuard {
+    cudaGraphExec_t* e;
+    ~ExecGuard() {
+      if (*e) cudaGraphExecDestroy(*e);
+    }
+  } exec_guard{&iter_exec};
   int outer = 0;
   long long inner = 0;
   double change = 0.0, res = 0.0;
@@ -573,21 +622,13 @@ fse_status ground_state(fse_plan* P, void* psi_v, void* ws, const fse_gs_opts& o
     double* hs = P->gs_host;
     int it = 0;
     for (; it < o.max_inner; ++it) {
-      if ((st = G.template update<GS_P>(G.p, G.r, G.v)) != FSE_OK) return st;
-      if ((st = G.matvec(G.p, G.v)) != FSE_OK) return st;
-      if ((st = G.dot2_dev(G.rh, G.v, G.rh, G.v)) != FSE_OK) return st;
-      k_gs_sc_alpha<<<1, 1, 0, G.st>>>(G.sc, G.out);
-      if ((st = G.chk("ground state scalars")) != FSE_OK) return st;
-      if ((st = G.template update<GS_S>(G.s, G.r, G.v)) != FSE_OK) return st;
-      if ((st = G.matvec(G.s, G.t)) != FSE_OK) return st;
-      if ((st = G.dot2_dev(G.t, G.s, G.t, G.t)) != FSE_OK) return st;
-      k_gs_sc_omega<<<1, 1, 0, G.st>>>(G.sc, G.out);
-      if ((st = G.chk("ground state scalars")) != FSE_OK) return st;
-      if ((st = G.template update<GS_X>(x, G.p, G.s)) != FSE_OK) return st;
-      if ((st = G.template update<GS_R>(G.r, G.s, G.t)) != FSE_OK) return st;
-      if ((st = G.dot2_dev(G.rh, G.r, G.r, G.r)) != FSE_OK) return st;
-      k_gs_sc_rho<<<1, 1, 0, G.st>>>(G.sc, G.out);
-      if ((st = G.chk("ground state scalars")) != FSE_OK) return st;
+      if (iter_exec) {
+        cudaError_t e = cudaGraphLaunch(iter_exec, G.st);
+        if (e != cudaSuccess) return cuda_fail(P, e, "ground state iteration");
+        P->launches += iter_launches;
+      } else if ((st = iteration()) != FSE_OK) {
+        return st;
+      }
       cudaError_t e = cudaMemcpyAsync(hs + (it & 1) * SC_SIZE, G.sc, sizeof(double) * SC_SIZE,
                                       cudaMemcpyDeviceToHost, G.st);
       if (e == cudaSuccess) e = cudaEventRecord(P->gs_ev[it & 1], G.st);
@@ -658,8 +699,27 @@ extern "C" fse_status fse_ground_state(fse_plan_t P, void* psi, void* workspace,
     cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_fail(P, e, "ground state events");
   }
-  return P->prec == FSE_F32 ? ground_state<float>(P, psi, workspace, *opts, info)
-                            : ground_state<double>(P, psi, workspace, *opts, info);
+  if (!P->gs_stream) {
+    cudaError_t e = cudaStreamCreateWithFlags(&P->gs_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->gs_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->gs_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(P, e, "ground state stream");
+  }
+  // the solve runs on a stream of the plan's own (capturable, unlike the
+  // legacy default stream), after and before the caller's stream
+  cudaStream_t user = P->stream;
+  cudaError_t e = cudaEventRecord(P->gs_fork, user);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->gs_stream, P->gs_fork, 0);
+  if (e != cudaSuccess) return cuda_fail(P, e, "ground state fork");
+  P->stream = P->gs_stream;
+  const fse_status st = P->prec == FSE_F32 ? ground_state<float>(P, psi, workspace, *opts, info)
+                                           : ground_state<double>(P, psi, workspace, *opts, info);
+  P->stream = user;
+  e = cudaEventRecord(P->gs_join, P->gs_stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(user, P->gs_join, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(user);
+  if (st == FSE_OK && e != cudaSuccess) return cuda_fail(P, e, "ground state join");
+  return st;
 }
 
 extern "C" fse_status fse_shift_kick(fse_plan_t P, void* psi, const double* x0, const double* k) {

@@ -44,6 +44,10 @@ struct fse_plan {
   // the first fse_ground_state call, released by fse_plan_destroy)
   double* gs_host = nullptr;
   cudaEvent_t gs_ev[2] = {nullptr, nullptr};
+  // the stream the solve runs on (its BiCGStab iteration is captured as a
+  // graph, which the legacy default stream does not allow) and its fork/join events
+  cudaStream_t gs_stream = nullptr;
+  cudaEvent_t gs_fork = nullptr, gs_join = nullptr;
 
   void* ws = nullptr;
   bool precomputed = false;
