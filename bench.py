@@ -197,8 +197,9 @@ def step_model_bytes(d: dict) -> int:
 
 # sources that define the split step's kernels and their launch arguments; the
 # DRAM counters in profiles/traffic.json stand only while these are unchanged
-STEP_SOURCES = ("fse_api.cu", "fse_col_f32.cu", "fse_col_f64.cu", "fse_fft.cuh", "fse_internal.h",
-                "fse_launch.cuh", "fse_passes.cuh", "fse_precompute.cu", "fse_x_f32.cu", "fse_x_f64.cu")
+STEP_SOURCES = ("fse_api.cu", "fse_col_f32.cu", "fse_col_f64.cu", "fse_fft.cuh", "fse_fft_x2.cuh", "fse_internal.h",
+                "fse_launch.cuh", "fse_passes.cuh", "fse_precompute.cu", "fse_x_f32.cu", "fse_x_f64.cu",
+                "fse_xpass_x2.cuh")
 
 
 def source_hash() -> str:

@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["fse_api.cu", "fse_precompute.cu", "fse_observables.cu", "fse_adjoint.cu",
            "fse_col_f32.cu", "fse_col_f64.cu", "fse_x_f32.cu", "fse_x_f64.cu", "fse_noalloc.cu",
            "fse_batch.cu", "fse_ground.cu"]
-HEADERS = ["fse_fft.cuh", "fse_fft_x2.cuh", "fse_passes.cuh", "fse_launch.cuh", "fse_internal.h"]
+HEADERS = ["fse_fft.cuh", "fse_fft_x2.cuh", "fse_xpass_x2.cuh", "fse_passes.cuh", "fse_launch.cuh", "fse_internal.h"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]

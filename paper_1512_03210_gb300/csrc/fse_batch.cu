@@ -75,7 +75,7 @@ k_xpass_batch(XArgs a, const typename Cplx<Real>::T* __restrict__ twn, const typ
     a.lam = r.lam;
     fill_f32_phase(a);
   }
-  xpass_body<Real, NX, KIND>(a, twn, tw2n, blockIdx.x);
+  xpass_any<Real, NX, KIND>(a, twn, tw2n, blockIdx.x);
 }
 
 template <int N, int VAR>

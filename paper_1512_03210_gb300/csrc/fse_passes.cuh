@@ -1198,10 +1198,28 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
   }
 }
 
+}  // namespace fse
+
+#include "fse_xpass_x2.cuh"
+
+namespace fse {
+
+// An x pass: the packed two-line code where it applies (fse_xpass_x2.cuh),
+// the one-line code otherwise.
+template <typename Real, int NX, int KIND>
+__device__ __forceinline__ void xpass_any(const XArgs& a, const typename Cplx<Real>::T* __restrict__ twn,
+                                          const typename Cplx<Real>::T* __restrict__ tw2n, int bid) {
+  if constexpr (sizeof(Real) == 4 && xpass_x2_ok<NX>() &&
+                (KIND == XP_FWD || KIND == XP_INV || KIND == XP_E || KIND == XP_A))
+    xpass_body_x2<NX, KIND>(a, twn, tw2n, bid);
+  else
+    xpass_body<Real, NX, KIND>(a, twn, tw2n, bid);
+}
+
 template <typename Real, int NX, int KIND>
 __global__ void __launch_bounds__(XCfg<Real, NX>::NT, XCfg<Real, NX>::MINB)
 k_xpass(XArgs a, const typename Cplx<Real>::T* __restrict__ twn, const typename Cplx<Real>::T* __restrict__ tw2n) {
-  xpass_body<Real, NX, KIND>(a, twn, tw2n, blockIdx.x);
+  xpass_any<Real, NX, KIND>(a, twn, tw2n, blockIdx.x);
 }
 
 // Host-side launchers (explicitly instantiated per precision).

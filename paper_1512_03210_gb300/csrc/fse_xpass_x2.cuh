@@ -1,0 +1,323 @@
+// fse_xpass_x2.cuh -- the float x passes on pairs of lines with packed
+// two-lane arithmetic (the line counterpart of the column passes of
+// fse_fft_x2.cuh).
+//
+// A tile of 16 consecutive lines (rows of psi) is held in shared memory as
+// 16-byte slots, slot (position j, pair p) = (re of line 2p, re of line
+// 2p + 1, im of line 2p, im of line 2p + 1): every Stockham pass moves whole
+// slots and does the butterfly of both lines of a pair (which share position
+// and twiddle) in one packed instruction per scalar operation. The zero-padded
+// transforms of the density (length 2 n_x, two real lines per complex line)
+// use the same slots for pairs of complex lines, 4 slots per row.
+//
+// Bank layout: a row of 8 slots is 128 bytes, and slot p of row j sits at
+// column p ^ (j & 7), so that both the Stockham passes (a quarter warp reads
+// the 8 slots of one row) and the transposing loads and stores (a quarter
+// warp touches one slot in each of 8 consecutive rows) are conflict-free. A
+// row of 4 slots is 64 bytes: rows are permuted (row j stored at
+// j ^ ((j >> 3) & 1), so that the two rows a quarter warp writes in a first
+// radix-8 pass fall on different bank halves) and slot p sits at column
+// p ^ ((j >> 1) & 3).
+//
+// Each thread owns one position x of the 256-point lines (x = thread index)
+// and all 8 pairs there. Used for the float passes X0 (forward x), XI (inverse
+// x), E (inverse x, density, zero-padded R2C) and A (cropped C2R, potential
+// phase, forward x) at n_x = 256 with 16-line tiles; other passes and sizes
+// run the one-line code (xpass_body).
+#pragma once
+
+#include "fse_fft_x2.cuh"
+
+namespace fse {
+
+template <int NX>
+struct XCfg2 {
+  static constexpr int NCOL = 16, NP = 8, NP2 = 4, NT = 256;
+  static_assert(NX == NT, "one position per thread");
+  static constexpr int PERP = NP;            // pairs per thread (all pairs at position x)
+  static constexpr int NH = NP2 * (NX + 1);  // (complex-line pair, bin) items of the half spectrum
+  static constexpr int PH = (NH + NT - 1) / NT;
+};
+
+template <int NX> __host__ __device__ constexpr bool xpass_x2_ok() {
+  return NX == 256 && ncol_for(2 * NX, 8) == 16;
+}
+
+// slot of (row, pair) in a tile of NP = 8 or NP = 4 slots per row (see above)
+template <int NP> __device__ __forceinline__ int pslot(int row, int p) {
+  static_assert(NP == 8 || NP == 4, "slot layouts");
+  if constexpr (NP == 8) return row * 8 + (p ^ (row & 7));
+  else return (row ^ ((row >> 3) & 1)) * 4 + (p ^ ((row >> 1) & 3));
+}
+
+__device__ __forceinline__ P2 p2_lds(const float4* buf, int s) {
+  const float4 t = buf[s];
+  return {make_float2(t.x, t.y), make_float2(t.z, t.w)};
+}
+__device__ __forceinline__ void p2_sts(float4* buf, int s, const P2& v) {
+  buf[s] = make_float4(v.re.x, v.re.y, v.im.x, v.im.y);
+}
+
+// One radix-R Stockham pass over NP pair-slots per row of a length-N tile in
+// shared memory (reads before a barrier, writes after it). ZIN: rows >= N/2
+// of the input are zero and not read; ZOUT: rows >= N/2 of the output are not stored.
+template <int N, int NP, int NT, int DIR, bool EXACT, int R, int NS, bool ZIN, bool ZOUT>
+__device__ __forceinline__ void pstockham_pass(float4* buf, const float4* __restrict__ twb) {
+  constexpr int ITEMS = NP * (N / R);
+  constexpr int PER = (ITEMS + NT - 1) / NT;
+  const int tid = threadIdx.x;
+  P2 v[PER][R];
+#pragma unroll
+  for (int it = 0; it < PER; ++it) {
+    const int w = tid + it * NT;
+    if ((ITEMS % NT) == 0 || w < ITEMS) {
+      const int g = w % NP, j = w / NP;
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (!(ZIN && 2 * r >= R)) v[it][r] = p2_lds(buf, pslot<NP>(j + r * (N / R), g));
+      if constexpr (NS > 1) {
+        const int k = j % NS;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[it][r] = ptwiddle<DIR, EXACT>(v[it][r], twb, (k * r) * (N / (NS * R)));
+      }
+      pdft<R, DIR, EXACT, ZIN>(v[it]);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < PER; ++it) {
+    const int w = tid + it * NT;
+    if ((ITEMS % NT) == 0 || w < ITEMS) {
+      const int g = w % NP, j = w / NP;
+      const int base = (j / NS) * NS * R + j % NS;
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (!(ZOUT && 2 * r >= R)) p2_sts(buf, pslot<NP>(base + r * NS, g), v[it][r]);
+    }
+  }
+  __syncthreads();
+}
+
+template <int N, int NP, int NT, int DIR, bool EXACT, int PASS, int NS, bool ZIN, bool ZOUT>
+__device__ __forceinline__ void pstockham_rec(float4* buf, const float4* __restrict__ twb) {
+  constexpr RadixPlan P = radix_plan(N);
+  if constexpr (PASS < P.npass) {
+    constexpr int R = P.r[PASS];
+    pstockham_pass<N, NP, NT, DIR, EXACT, R, NS, ZIN && PASS == 0, ZOUT && PASS + 1 == P.npass>(buf, twb);
+    pstockham_rec<N, NP, NT, DIR, EXACT, PASS + 1, NS * R, ZIN, ZOUT>(buf, twb);
+  }
+}
+
+// Transform of the NP pairs of lines of length N held in buf (the caller
+// synchronised before; the call ends with a barrier). The 4-slot layout's row
+// permutation keeps a first radix-8 pass conflict-free.
+template <int N, int NP, int NT, int DIR, bool EXACT, bool ZIN = false, bool ZOUT = false>
+__device__ __forceinline__ void pfft_tile(float4* buf, const float4* __restrict__ twb) {
+  static_assert((N & (N - 1)) == 0 && N >= 32 && radix_plan(N).r[0] == 8, "packed x transforms: radix-8 first pass");
+  pstockham_rec<N, NP, NT, DIR, EXACT, 0, 1, ZIN, ZOUT>(buf, twb);
+}
+
+// Densities of the tile's lines (rho[p] = lines 2p, 2p + 1 at this thread's
+// position x) -> x-half-spectra of the zero-padded lines in S. Two real lines
+// form one complex line (line 2p real part, 2p + 1 imaginary part), two
+// complex lines one slot; one packed FFT of length 2 NX; the spectra are
+// separated with A_k = (Z_k + conj Z_-k)/2, B_k = (Z_k - conj Z_-k)/(2i).
+// The caller has synchronised (buf free); ends without a barrier.
+template <int NX>
+__device__ __forceinline__ void r2c_rows_x2(const XArgs& a, float4* buf, int l0, const float4* __restrict__ twb2,
+                                            const float2 (&rho)[XCfg2<NX>::PERP]) {
+  typedef XCfg2<NX> K;
+  constexpr int NP2 = K::NP2, NT = K::NT;
+  const int tid = threadIdx.x, x = tid;
+#pragma unroll
+  for (int q = 0; q < NP2; ++q)
+    buf[pslot<NP2>(x, q)] = make_float4(rho[2 * q].x, rho[2 * q + 1].x, rho[2 * q].y, rho[2 * q + 1].y);
+  // rows NX..2NX-1 are the zero padding: the first (radix-8) pass does not read them
+  __syncthreads();
+  pfft_tile<2 * NX, NP2, NT, -1, false, true, false>(buf, twb2);
+  float2* S = reinterpret_cast<float2*>(a.spec);
+  const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
+  const float2 half = bc(0.5f);
+#pragma unroll
+  for (int it = 0; it < K::PH; ++it) {
+    const int idx = tid + it * NT;
+    if (idx < K::NH) {
+      const int q = idx / (NX + 1), k = idx % (NX + 1);
+      const P2 zk = p2_lds(buf, pslot<NP2>(k, q));
+      const P2 zm = p2_lds(buf, pslot<NP2>((2 * NX - k) % (2 * NX), q));
+      const float2 ar = mul2(half, add2(zk.re, zm.re)), ai = mul2(half, sub2(zk.im, zm.im));
+      const float2 br = mul2(half, add2(zk.im, zm.im)), bi = mul2(half, sub2(zm.re, zk.re));
+      // complex line 2q + c carries real lines 4q + 2c (A) and 4q + 2c + 1 (B)
+      const int lb = 4 * q;
+      const float2 vals[4] = {make_float2(ar.x, ai.x), make_float2(br.x, bi.x), make_float2(ar.y, ai.y),
+                              make_float2(br.y, bi.y)};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (l0 + lb + u < a.nlines) S[srow(y0, z0, lb + u, a.ny, a.srow_mul) * a.sx + k] = vals[u];
+    }
+  }
+}
+
+// x-half-spectra in S of the tile's lines -> real values val[p] of lines 2p,
+// 2p + 1 at this thread's position x (cropped C2R of length 2 NX, two complex
+// lines per slot via the Hermitian extension Z = A + i B). The caller has
+// synchronised (buf free); ends after the values are read (the caller
+// synchronises before reusing buf).
+template <int NX>
+__device__ __forceinline__ void c2r_rows_x2(const XArgs& a, float4* buf, int l0, const float4* __restrict__ twb2,
+                                            float2 (&val)[XCfg2<NX>::PERP]) {
+  typedef XCfg2<NX> K;
+  constexpr int NP2 = K::NP2, NT = K::NT;
+  const int tid = threadIdx.x, x = tid;
+  const float2* S = reinterpret_cast<const float2*>(a.spec);
+  const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
+#pragma unroll
+  for (int it = 0; it < K::PH; ++it) {
+    const int idx = tid + it * NT;
+    if (idx < K::NH) {
+      const int q = idx / (NX + 1), k = idx % (NX + 1);
+      const int lb = 4 * q;
+      float2 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        v[u] = (l0 + lb + u < a.nlines) ? S[srow(y0, z0, lb + u, a.ny, a.srow_mul) * a.sx + k] : make_float2(0.f, 0.f);
+      // lane c: A = v[2c], B = v[2c + 1]; Z_k = A + i B, Z_{2NX-k} = conj(A) + i conj(B)
+      const P2 zk{make_float2(v[0].x - v[1].y, v[2].x - v[3].y), make_float2(v[0].y + v[1].x, v[2].y + v[3].x)};
+      p2_sts(buf, pslot<NP2>(k, q), zk);
+      if (k > 0 && k < NX) {
+        const P2 zm{make_float2(v[0].x + v[1].y, v[2].x + v[3].y), make_float2(v[1].x - v[0].y, v[3].x - v[2].y)};
+        p2_sts(buf, pslot<NP2>(2 * NX - k, q), zm);
+      }
+    }
+  }
+  __syncthreads();
+  // only rows 0..NX-1 survive the crop: the last pass stores no others
+  pfft_tile<2 * NX, NP2, NT, +1, false, false, true>(buf, twb2);
+#pragma unroll
+  for (int q = 0; q < NP2; ++q) {
+    const float4 t = buf[pslot<NP2>(x, q)];
+    val[2 * q] = make_float2(t.x, t.z);
+    val[2 * q + 1] = make_float2(t.y, t.w);
+  }
+}
+
+// sin and cos of the phases of two lines: the short series of phase_sincos
+// in packed form when both are within 1/2, sincosf otherwise.
+__device__ __forceinline__ void phase_sincos2(float2 th, float2& sn, float2& cs) {
+  if (fabsf(th.x) <= 0.5f && fabsf(th.y) <= 0.5f) {
+    const float2 t2 = mul2(th, th);
+    const float2 ps = mul2(t2, fma2(t2, fma2(t2, fma2(t2, bc(1.0f / 362880.0f), bc(-1.0f / 5040.0f)), bc(1.0f / 120.0f)),
+                                    bc(-1.0f / 6.0f)));
+    const float2 pc = mul2(t2, fma2(t2, fma2(t2, fma2(t2, bc(1.0f / 40320.0f), bc(-1.0f / 720.0f)), bc(1.0f / 24.0f)),
+                                    bc(-0.5f)));
+    sn = fma2(th, ps, th);
+    cs = add2(bc(1.0f), pc);
+  } else {
+    phase_sincos(th.x, &sn.x, &cs.x);
+    phase_sincos(th.y, &sn.y, &cs.y);
+  }
+}
+
+template <int NX, int KIND>
+__device__ __forceinline__ void xpass_body_x2(const XArgs& a, const float2* __restrict__ twn,
+                                              const float2* __restrict__ tw2n, int bid) {
+  typedef XCfg2<NX> K;
+  constexpr int NCOL = K::NCOL, NP = K::NP, NT = K::NT;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double red[32];
+  float4* buf = reinterpret_cast<float4*>(smem_raw);
+  const float4* twb1 = twb_of<NX>(twn);
+  const float4* twb2 = twb_of<2 * NX>(tw2n);
+  const int tid = threadIdx.x, x = tid;
+  const int l0 = bid * NCOL;
+  float2* psi = reinterpret_cast<float2*>(a.psi) + (long long)l0 * NX + x;  // line l0 at position x
+  const int nl = a.nlines - l0;  // lines of this tile that exist (may exceed NCOL)
+  const float2 z = make_float2(0.f, 0.f);
+
+  if constexpr (KIND == XP_FWD || KIND == XP_INV || KIND == XP_E) {
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const float2 u0 = 2 * p < nl ? psi[(2 * p) * NX] : z;
+      const float2 u1 = 2 * p + 1 < nl ? psi[(2 * p + 1) * NX] : z;
+      p2_sts(buf, pslot<NP>(x, p), P2{make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)});
+    }
+    __syncthreads();
+    pfft_tile<NX, NP, NT, (KIND == XP_FWD ? -1 : +1), true>(buf, twb1);
+    float2 rho[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const P2 u = p2_lds(buf, pslot<NP>(x, p));
+      if (2 * p < nl) psi[(2 * p) * NX] = make_float2(u.re.x, u.im.x);
+      if (2 * p + 1 < nl) psi[(2 * p + 1) * NX] = make_float2(u.re.y, u.im.y);
+      rho[p] = fma2(u.re, u.re, mul2(u.im, u.im));
+    }
+    if constexpr (KIND == XP_E || KIND == XP_INV) {
+      if (a.part) {  // float64 mass partial of this tile (renormalisation)
+        double acc = 0.0;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) acc += (double)rho[p].x + (double)rho[p].y;
+        acc = block_sum(acc, red);
+        if (tid == 0) a.part[bid] = acc;
+      }
+    }
+    if constexpr (KIND == XP_E) {
+      __syncthreads();
+      r2c_rows_x2<NX>(a, buf, l0, twb2, rho);
+    }
+  } else {
+    static_assert(KIND == XP_A, "packed x passes: X0, XI, E, A");
+    if (tid == 0 && nl > 0 && (reinterpret_cast<uintptr_t>(a.psi) & 15) == 0) {
+      // the tile's rows of psi (contiguous) move to L2 while the C2R runs
+      prefetch_l2_bulk(reinterpret_cast<float2*>(a.psi) + (long long)l0 * NX,
+                       (unsigned)(min(NCOL, nl) * NX * sizeof(float2)));
+    }
+    float2 vphi[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) vphi[p] = z;
+    if (a.use_spec) c2r_rows_x2<NX>(a, buf, l0, twb2, vphi);
+    const bool rescale = a.scale != nullptr;
+    const float fsc = rescale ? float(*a.scale) : 1.0f;
+    const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
+    __syncthreads();
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const bool ok0 = 2 * p < nl, ok1 = 2 * p + 1 < nl;
+      const float2 u0 = ok0 ? psi[(2 * p) * NX] : z;
+      const float2 u1 = ok1 ? psi[(2 * p + 1) * NX] : z;
+      int ya, za, yb, zb;
+      line_yz(y0, z0, 2 * p, a.ny, ya, za);
+      line_yz(y0, z0, 2 * p + 1, a.ny, yb, zb);
+      const P2 u{make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
+      const float2 rho = fma2(u.re, u.re, mul2(u.im, u.im));
+      const float2 P = make_float2(trap_phase<float, 0>(a, x, ya, za), trap_phase<float, 0>(a, x, yb, zb));
+      const float2 th = fma2(bc(a.f.beta_dt), rho, fma2(bc(a.f.lam), vphi[p], P));
+      float2 sn, cs;
+      phase_sincos2(th, sn, cs);
+      // u2 = u (cs - i sn), the factor's modulus error folded in (unit_mul)
+      const float2 h = make_float2(-0.5f * norm_err(cs.x, sn.x), -0.5f * norm_err(cs.y, sn.y));
+      const float2 s2 = neg2(sn);
+      const float2 lc = mul2(h, cs), ls = mul2(h, s2);
+      const float2 lr = fma2(u.re, lc, mul2(u.im, neg2(ls)));
+      const float2 li = fma2(u.re, ls, mul2(u.im, lc));
+      float2 yr = fma2(u.re, cs, fma2(u.im, neg2(s2), lr));
+      float2 yi = fma2(u.re, s2, fma2(u.im, cs, li));
+      if (rescale) {
+        yr = mul2(bc(fsc), yr);
+        yi = mul2(bc(fsc), yi);
+      }
+      if (!ok0) yr.x = yi.x = 0.f;
+      if (!ok1) yr.y = yi.y = 0.f;
+      p2_sts(buf, pslot<NP>(x, p), P2{yr, yi});
+    }
+    __syncthreads();
+    pfft_tile<NX, NP, NT, -1, true>(buf, twb1);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const P2 u = p2_lds(buf, pslot<NP>(x, p));
+      if (2 * p < nl) psi[(2 * p) * NX] = make_float2(u.re.x, u.im.x);
+      if (2 * p + 1 < nl) psi[(2 * p + 1) * NX] = make_float2(u.re.y, u.im.y);
+    }
+  }
+}
+
+}  // namespace fse

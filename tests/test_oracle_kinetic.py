@@ -290,3 +290,42 @@ def test_fourth_order_reversible_and_free():
     got = O.evolve(phi, p, 0.1, 1)
     ex = np.fft.ifftn(np.exp(-0.5j * p.dt * O.kinetic_symbol(p)) * np.fft.fftn(phi))
     assert np.max(np.abs(got - ex)) < 1e-13
+
+
+def _naive_fft(x):
+    """Recursive mixed-radix decimation-in-time DFT (radix 2 and 3), twiddles
+    from math.cos / math.sin, written from the DFT's definition
+    X_k = sum_j x_j exp(-2 pi i j k / N)."""
+    n = len(x)
+    if n == 1:
+        return [complex(x[0])]
+    r = 2 if n % 2 == 0 else 3
+    assert n % r == 0
+    m = n // r
+    subs = [_naive_fft(x[q::r]) for q in range(r)]
+    out = [0j] * n
+    for k in range(n):
+        acc = 0j
+        for q in range(r):
+            a = -2.0 * math.pi * q * k / n
+            acc += subs[q][k % m] * complex(math.cos(a), math.sin(a))
+        out[k] = acc
+    return out
+
+
+@pytest.mark.parametrize("n", [8, 12, 48, 96, 256])
+def test_library_fft_matches_naive_recursive_fft(n):
+    """The oracle's one library primitive (numpy's FFT, forward unnormalised and
+    inverse 1/N, reading 6) against a naive recursive radix-2/3 FFT and, for the
+    short lengths, the O(N^2) sum of the DFT's definition."""
+    rng = np.random.default_rng(n)
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    ref = np.array(_naive_fft(list(x)))
+    got = np.fft.fft(x)
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    back = np.fft.ifft(got)
+    assert np.max(np.abs(back - x)) <= 1e-13 * np.max(np.abs(x))
+    if n <= 48:
+        j = np.arange(n)
+        dft = np.exp(-2j * np.pi * np.outer(j, j) / n) @ x
+        assert np.max(np.abs(got - dft)) <= 1e-12 * np.max(np.abs(dft))
