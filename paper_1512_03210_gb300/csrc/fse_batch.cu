@@ -38,7 +38,7 @@ __device__ __forceinline__ double sin_over_dev(double a, double d) {
 }
 
 template <typename Real, int N, int VAR>
-__global__ void __launch_bounds__(ColCfg<Real, N>::NT, ColCfg<Real, N>::MINB)
+__global__ void __launch_bounds__(ColCfg<Real, N, VAR>::NT, ColCfg<Real, N, VAR>::MINB)
 k_colpass_batch(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__ tw, const BatchRun* runs,
                 int on_spec, int kin_full, int conj) {
   const BatchRun r = runs[blockIdx.y];
@@ -81,7 +81,7 @@ k_xpass_batch(XArgs a, const typename Cplx<Real>::T* __restrict__ twn, const typ
 template <int N, int VAR>
 static cudaError_t colb(const ColArgs& a, const MulArgs& m, const void* tw, const BatchRun* runs, int nr,
                         int on_spec, int kin_full, int conj, cudaStream_t st) {
-  typedef ColCfg<float, N> K;
+  typedef ColCfg<float, N, VAR> K;
   const size_t smem = K::smem_bytes(VAR);
   static std::atomic<unsigned long long> done{0};
   cudaError_t e = allow_smem(k_colpass_batch<float, N, VAR>, smem, done);

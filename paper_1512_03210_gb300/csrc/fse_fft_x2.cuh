@@ -174,8 +174,29 @@ __device__ __forceinline__ void pregs_pass(P2 (&v)[W], const float4* __restrict_
     if constexpr (NS > 1) {
       const int j = (tid + i * NT) / NCP;
       const int k = j % NS;
+      if constexpr (EXACT) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[i * R + r] = ptwiddle<DIR, EXACT>(v[i * R + r], twb, (k * r) * (N / (NS * R)));
+        for (int r = 1; r < R; ++r) v[i * R + r] = ptwiddle<DIR, EXACT>(v[i * R + r], twb, (k * r) * (N / (NS * R)));
+      } else {
+        // transforms of the density: twiddle r as the r-th power of twiddle 1
+        // (one table load instead of R - 1; the powers drift by ~r ulp, far
+        // below what a density spectrum that only sets a phase notices), so
+        // that only two twiddles are ever live in registers
+        const float4 w = __ldg(&twb[2 * (k * (N / (NS * R)))]);
+        const float2 c1 = make_float2(w.x, w.y), s1 = make_float2(w.z, w.w);
+        float2 c = c1, sn = s1;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          if (r > 1) {
+            const float2 cn = fma2(c, c1, mul2(sn, neg2(s1)));
+            sn = fma2(c, s1, mul2(sn, c1));
+            c = cn;
+          }
+          const P2 x = v[i * R + r];
+          v[i * R + r] = DIR < 0 ? P2{fma2(x.im, neg2(sn), mul2(x.re, c)), fma2(x.im, c, mul2(x.re, sn))}
+                                 : P2{fma2(x.im, sn, mul2(x.re, c)), fma2(x.re, neg2(sn), mul2(x.im, c))};
+        }
+      }
     }
     pdft<R, DIR, EXACT, ZIN>(&v[i * R]);
   }

@@ -28,7 +28,7 @@ static cudaError_t allow_smem(F* fn, size_t bytes, std::atomic<unsigned long lon
 
 template <typename Real, int N, int VAR>
 static cudaError_t col_launch(const ColArgs& a, const MulArgs& m, const void* tw, cudaStream_t st) {
-  typedef ColCfg<Real, N> K;
+  typedef ColCfg<Real, N, VAR> K;
   typedef typename K::C C;
   const size_t smem = K::smem_bytes(VAR);
   static std::atomic<unsigned long long> done{0};

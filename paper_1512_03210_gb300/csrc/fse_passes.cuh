@@ -193,7 +193,14 @@ enum { COL_FWD = 0, COL_INV = 1, COL_PADF = 2, COL_CROPI = 3, COL_KIN = 4, COL_K
 
 __host__ __device__ constexpr int col_ncol(int N, int csize) { return ncol_for(N, csize); }
 
-template <typename Real, int N>
+// Threads per tile of a packed (pair) column pass: 256 by default, so that a
+// long transform keeps two items per thread and registers for them; the
+// zero-padded forward (F) and cropped inverse (H) transforms of the density,
+// one transform each and no multiplier, fit 512 threads of one item without
+// spilling and run faster with the extra warps.
+__host__ __device__ constexpr int x2_maxt(int var) { return (var == 2 || var == 3) ? 512 : 256; }
+
+template <typename Real, int N, int VAR = -1>
 struct ColCfg {
   typedef typename Cplx<Real>::T C;
   static constexpr int NCOL = col_ncol(N, sizeof(C));
@@ -205,12 +212,7 @@ struct ColCfg {
   // and the 8 threads of a quarter warp always touch the NCOL / 2 slots of one
   // row, so pairs need no padding; single columns pad to NCOL + 1
   static constexpr int LDS = CW == 2 ? NCOL : NCOL + 1;
-#ifndef FSE_X2_MAXT
-#define FSE_X2_MAXT 256
-#endif
-  // packed pairs (CW = 2): at most FSE_X2_MAXT threads per tile, so that a
-  // long transform keeps two items per thread and the registers for them
-  static constexpr int MAXT = CW == 2 ? FSE_X2_MAXT : 512;
+  static constexpr int MAXT = CW == 2 ? x2_maxt(VAR) : 512;
   static constexpr int E = reg_elems(N, NCOL, CW, MAXT);
   static constexpr int NT = reg_threads(N, NCOL, CW, MAXT);
   static constexpr int R0 = radix_plan(N).r[0];
@@ -236,7 +238,7 @@ struct ColCfg {
 template <typename Real, int N, int VAR, bool GATHER>
 __device__ __forceinline__ void colpass_tile(const ColArgs& a, const MulArgs& m,
                                              const typename Cplx<Real>::T* __restrict__ tw, int bid, int ngat) {
-  typedef ColCfg<Real, N> K;
+  typedef ColCfg<Real, N, VAR> K;
   typedef typename K::C C;
   constexpr int NCOL = K::NCOL, NCP = K::NCP, CW = K::CW, LDS = K::LDS, NT = K::NT, E = K::E;
   constexpr int R0 = K::R0, RL = K::RL;
@@ -510,7 +512,7 @@ struct X2Geo {
 
 template <int N, int VAR, bool GATHER>
 __device__ __forceinline__ void x2_geo(const ColArgs& a, const MulArgs& m, int bid, int ngat, X2Geo& g, int tid) {
-  typedef ColCfg<float, N> K;
+  typedef ColCfg<float, N, VAR> K;
   constexpr int NCOL = K::NCOL, NCP = K::NCP;
   const int cg = tid % NCP;  // this thread's columns of the tile: 2 cg, 2 cg + 1
   const int breg = bid - ngat;
@@ -565,7 +567,7 @@ __device__ __forceinline__ void x2_store_row(const ColArgs& a, const X2Geo& g, i
 // Row of the first-pass input c of this thread (items i, radix index r; the
 // zero half of a padded line is never read), c < ColCfg::first(VAR).
 template <int N, int VAR> __device__ __forceinline__ int x2_first_row(int c, int tid) {
-  typedef ColCfg<float, N> K;
+  typedef ColCfg<float, N, VAR> K;
   constexpr int RH = K::rh(VAR);
   const int i = c / RH, r = c % RH;
   return (tid + i * K::NT) / K::NCP + r * (N / K::R0);
@@ -573,9 +575,9 @@ template <int N, int VAR> __device__ __forceinline__ int x2_first_row(int c, int
 
 // The first pass's inputs into registers, straight from global memory.
 template <int N, int VAR>
-__device__ __forceinline__ void x2_first_loads(const ColArgs& a, const X2Geo& g, P2 (&v)[ColCfg<float, N>::E / 2],
+__device__ __forceinline__ void x2_first_loads(const ColArgs& a, const X2Geo& g, P2 (&v)[ColCfg<float, N, VAR>::E / 2],
                                                int tid) {
-  typedef ColCfg<float, N> K;
+  typedef ColCfg<float, N, VAR> K;
   constexpr int RH = K::rh(VAR), R0 = K::R0;
 #pragma unroll
   for (int c = 0; c < K::first(VAR); ++c) {
@@ -589,7 +591,7 @@ __device__ __forceinline__ void x2_first_loads(const ColArgs& a, const X2Geo& g,
 template <int N, int VAR, bool GATHER>
 __device__ __forceinline__ void x2_chat_issue(const ColArgs& a, const MulArgs& m, const X2Geo& g, int bid,
                                               float* sC, int tid) {
-  typedef ColCfg<float, N> K;
+  typedef ColCfg<float, N, VAR> K;
   constexpr int NCOL = K::NCOL, NT = K::NT;
   const float* ch = reinterpret_cast<const float*>(m.chat);
   if (!GATHER) {
@@ -624,8 +626,8 @@ __device__ __forceinline__ void x2_chat_issue(const ColArgs& a, const MulArgs& m
 // copies are the second most recent cp.async group of this thread.
 template <int N, int VAR>
 __device__ __forceinline__ void x2_compute(const ColArgs& a, const MulArgs& m, const float2* __restrict__ tw,
-                                           const X2Geo& g, P2 (&v)[ColCfg<float, N>::E / 2], int tid) {
-  typedef ColCfg<float, N> K;
+                                           const X2Geo& g, P2 (&v)[ColCfg<float, N, VAR>::E / 2], int tid) {
+  typedef ColCfg<float, N, VAR> K;
   constexpr int NCOL = K::NCOL, NCP = K::NCP, LDS = K::LDS, NT = K::NT, W = K::E / 2;
   constexpr int R0 = K::R0, RL = K::RL;
   constexpr bool FUSED = (VAR == COL_KIN || VAR == COL_KHAT) && plan_palindrome(N);
@@ -742,7 +744,7 @@ __device__ __forceinline__ void x2_compute(const ColArgs& a, const MulArgs& m, c
 template <int N, int VAR, bool GATHER>
 __device__ __forceinline__ void colpass_tile_x2(const ColArgs& a, const MulArgs& m, const float2* __restrict__ tw,
                                                 int bid, int ngat) {
-  typedef ColCfg<float, N> K;
+  typedef ColCfg<float, N, VAR> K;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tid = threadIdx.x;
   X2Geo g;
@@ -769,8 +771,8 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
   // only passes over R2C bins (ncols = nx + 1) have tail tiles; they come
   // first in the grid, so that they overlap the full tiles
   constexpr bool TAILS = (VAR == COL_PADF || VAR == COL_CROPI || VAR == COL_KHAT);
-  constexpr bool X2 = ColCfg<Real, N>::CW == 2;  // float pairs: packed arithmetic
-  constexpr int NCOL = ColCfg<Real, N>::NCOL;
+  constexpr bool X2 = ColCfg<Real, N, VAR>::CW == 2;  // float pairs: packed arithmetic
+  constexpr int NCOL = ColCfg<Real, N, VAR>::NCOL;
   const int ngat = (TAILS && a.tail > 0) ? (a.nplanes * a.tail + NCOL - 1) / NCOL : 0;
   if constexpr (X2 && TAILS) {
     if (bid < ngat) colpass_tile_x2<N, VAR, true>(a, m, tw, bid, ngat);
@@ -786,7 +788,7 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
 }
 
 template <typename Real, int N, int VAR>
-__global__ void __launch_bounds__(ColCfg<Real, N>::NT, ColCfg<Real, N>::MINB)
+__global__ void __launch_bounds__(ColCfg<Real, N, VAR>::NT, ColCfg<Real, N, VAR>::MINB)
 k_colpass(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__ tw) {
   colpass_body<Real, N, VAR>(a, m, tw, blockIdx.x);
 }
