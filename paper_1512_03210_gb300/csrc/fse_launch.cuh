@@ -11,6 +11,24 @@ namespace fse {
 #define FSE_COL_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
 #define FSE_X_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
 
+// Launch of a step pass with programmatic dependent launch on the previous
+// kernel in the stream (see pass_prologue).
+template <typename... Params, typename... Args>
+static cudaError_t launch_pass(void (*kernel)(Params...), unsigned blocks, unsigned threads, size_t smem,
+                               cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // cudaFuncSetAttribute once per kernel and device when the dynamic tile comes
 // near the 48 KB default (the kernels also hold up to 1 KB of static shared memory).
 template <typename F>
@@ -39,8 +57,7 @@ static cudaError_t col_launch(const ColArgs& a, const MulArgs& m, const void* tw
   if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
   MulArgs mf = m;
   fill_f32(mf);
-  k_colpass<Real, N, VAR><<<(unsigned)blocks, K::NT, smem, st>>>(a, mf, reinterpret_cast<const C*>(tw));
-  return cudaGetLastError();
+  return launch_pass(k_colpass<Real, N, VAR>, (unsigned)blocks, K::NT, smem, st, a, mf, reinterpret_cast<const C*>(tw));
 }
 
 template <typename Real>
@@ -79,9 +96,8 @@ static cudaError_t x_launch(const XArgs& a, const void* twn, const void* tw2n, c
   if (blocks <= 0) return cudaSuccess;
   XArgs af = a;
   fill_f32(af);
-  k_xpass<Real, NX, KIND><<<blocks, K::NT, smem, st>>>(af, reinterpret_cast<const C*>(twn),
-                                                       reinterpret_cast<const C*>(tw2n));
-  return cudaGetLastError();
+  return launch_pass(k_xpass<Real, NX, KIND>, (unsigned)blocks, K::NT, smem, st, af, reinterpret_cast<const C*>(twn),
+                     reinterpret_cast<const C*>(tw2n));
 }
 
 template <typename Real>

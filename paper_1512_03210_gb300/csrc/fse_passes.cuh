@@ -176,6 +176,18 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 __device__ __forceinline__ int wrap_index(int i, int L) { return i < (L >> 1) ? i : i - L; }
 
+// First statement of every step pass. The passes of a step are launched with
+// programmatic dependent launch: a block first waits until the previous pass
+// has completed and its writes are visible (griddepcontrol.wait; immediate
+// for a launch without that dependency), then lets the next pass be launched
+// (griddepcontrol.launch_dependents), so that the next pass's blocks are
+// scheduled onto SMs as this pass's last blocks finish instead of after a
+// launch gap. The next pass's blocks do nothing before their own wait.
+__device__ __forceinline__ void pass_prologue() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
 // ---------------------------------------------------------------------------
 // Column pass: transforms along a strided axis, tiles of NCOL adjacent columns.
 // Variants (VAR):
@@ -790,6 +802,7 @@ __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
 template <typename Real, int N, int VAR>
 __global__ void __launch_bounds__(ColCfg<Real, N, VAR>::NT, ColCfg<Real, N, VAR>::MINB)
 k_colpass(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__ tw) {
+  pass_prologue();
   colpass_body<Real, N, VAR>(a, m, tw, blockIdx.x);
 }
 
@@ -1221,6 +1234,7 @@ __device__ __forceinline__ void xpass_any(const XArgs& a, const typename Cplx<Re
 template <typename Real, int NX, int KIND>
 __global__ void __launch_bounds__(XCfg<Real, NX>::NT, XCfg<Real, NX>::MINB)
 k_xpass(XArgs a, const typename Cplx<Real>::T* __restrict__ twn, const typename Cplx<Real>::T* __restrict__ tw2n) {
+  pass_prologue();
   xpass_any<Real, NX, KIND>(a, twn, tw2n, blockIdx.x);
 }
 
