@@ -11,9 +11,10 @@
 // use the same slots for pairs of complex lines, 4 slots per row.
 //
 // Bank layout: a row of 8 slots is 128 bytes, and slot p of row j sits at
-// column p ^ (j & 7), so that both the Stockham passes (a quarter warp reads
-// the 8 slots of one row) and the transposing loads and stores (a quarter
-// warp touches one slot in each of 8 consecutive rows) are conflict-free. A
+// column p ^ ((j ^ (j >> 3)) & 7), so that the Stockham passes (a quarter warp
+// reads the 8 slots of one row), the transposing accesses (one slot in each
+// of 8 consecutive rows) and the first pass's writes (one slot in each of rows
+// 8j + r for 8 consecutive j) are all conflict-free. A
 // row of 4 slots is 64 bytes: rows are permuted (row j stored at
 // j ^ ((j >> 3) & 1), so that the two rows a quarter warp writes in a first
 // radix-8 pass fall on different bank halves) and slot p sits at column
@@ -46,7 +47,7 @@ template <int NX> __host__ __device__ constexpr bool xpass_x2_ok() {
 // slot of (row, pair) in a tile of NP = 8 or NP = 4 slots per row (see above)
 template <int NP> __device__ __forceinline__ int pslot(int row, int p) {
   static_assert(NP == 8 || NP == 4, "slot layouts");
-  if constexpr (NP == 8) return row * 8 + (p ^ (row & 7));
+  if constexpr (NP == 8) return row * 8 + (p ^ ((row ^ (row >> 3)) & 7));
   else return (row ^ ((row >> 3) & 1)) * 4 + (p ^ ((row >> 1) & 3));
 }
 
@@ -117,21 +118,55 @@ __device__ __forceinline__ void pfft_tile(float4* buf, const float4* __restrict_
   pstockham_rec<N, NP, NT, DIR, EXACT, 0, 1, ZIN, ZOUT>(buf, twb);
 }
 
-// Densities of the tile's lines (rho[p] = lines 2p, 2p + 1 at this thread's
-// position x) -> x-half-spectra of the zero-padded lines in S. Two real lines
-// form one complex line (line 2p real part, 2p + 1 imaginary part), two
-// complex lines one slot; one packed FFT of length 2 NX; the spectra are
-// separated with A_k = (Z_k + conj Z_-k)/2, B_k = (Z_k - conj Z_-k)/(2i).
-// The caller has synchronised (buf free); ends without a barrier.
+// The length-256 transforms of the lines (plan 8, 8, 4) with their first
+// pass on registers and their last pass into registers, so that the tile is
+// read from and written to global memory directly: thread t works on pair
+// g = t / 32 and positions j + 32 r (first pass, j = t % 32), and on pairs
+// 2 (t / 64) and 2 (t / 64) + 1 at positions j + 64 r (last pass, j = t % 64),
+// both coalesced along the lines.
+constexpr int XR_N = 256;
+static_assert(radix_plan(XR_N).npass == 3 && radix_plan(XR_N).r[0] == 8 && radix_plan(XR_N).r[1] == 8 &&
+                  radix_plan(XR_N).r[2] == 4,
+              "register first and last passes: plan 8, 8, 4");
+
+// First pass (radix 8, no twiddles) of the values v[r] at positions j + 32 r
+// of pair g, written to the tile (the caller synchronises after).
+template <int DIR, bool EXACT>
+__device__ __forceinline__ void pfirst_pass(float4* buf, P2 (&v)[8], int g, int j) {
+  pdft<8, DIR, EXACT, false>(v);
+#pragma unroll
+  for (int r = 0; r < 8; ++r) p2_sts(buf, pslot<8>(j * 8 + r, g), v[r]);
+}
+
+// Last pass (radix 4, twiddles j r) from the tile into registers: out[it][r]
+// holds position j + 64 r of pair g_it = 2 (t / 64) + it (j = t % 64).
+template <int DIR, bool EXACT>
+__device__ __forceinline__ void plast_pass(const float4* buf, const float4* __restrict__ twb, P2 (&out)[2][4], int tid) {
+  const int j = tid & 63;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int g = 2 * (tid >> 6) + it;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) out[it][r] = p2_lds(buf, pslot<8>(j + 64 * r, g));
+#pragma unroll
+    for (int r = 1; r < 4; ++r) out[it][r] = ptwiddle<DIR, EXACT>(out[it][r], twb, j * r);
+    pdft<4, DIR, EXACT, false>(out[it]);
+  }
+}
+
+// Densities of the tile's lines -> x-half-spectra of the zero-padded lines in
+// S. Two real lines form one complex line (line 2p real part, 2p + 1 imaginary
+// part), two complex lines one slot; one packed FFT of length 2 NX; the
+// spectra are separated with A_k = (Z_k + conj Z_-k)/2, B_k = (Z_k - conj
+// Z_-k)/(2i). Ends without a barrier.
+// The caller has written the densities into rows 0..NX-1 of the packed tile
+// (complex line c in lane c & 1 of slot c >> 1) and not synchronised.
 template <int NX>
-__device__ __forceinline__ void r2c_rows_x2(const XArgs& a, float4* buf, int l0, const float4* __restrict__ twb2,
-                                            const float2 (&rho)[XCfg2<NX>::PERP]) {
+__device__ __forceinline__ void r2c_rows_x2_staged(const XArgs& a, float4* buf, int l0,
+                                                   const float4* __restrict__ twb2) {
   typedef XCfg2<NX> K;
   constexpr int NP2 = K::NP2, NT = K::NT;
-  const int tid = threadIdx.x, x = tid;
-#pragma unroll
-  for (int q = 0; q < NP2; ++q)
-    buf[pslot<NP2>(x, q)] = make_float4(rho[2 * q].x, rho[2 * q + 1].x, rho[2 * q].y, rho[2 * q + 1].y);
+  const int tid = threadIdx.x;
   // rows NX..2NX-1 are the zero padding: the first (radix-8) pass does not read them
   __syncthreads();
   pfft_tile<2 * NX, NP2, NT, -1, false, true, false>(buf, twb2);
@@ -235,34 +270,58 @@ __device__ __forceinline__ void xpass_body_x2(const XArgs& a, const float2* __re
   const float2 z = make_float2(0.f, 0.f);
 
   if constexpr (KIND == XP_FWD || KIND == XP_INV || KIND == XP_E) {
+    constexpr int DIR = KIND == XP_FWD ? -1 : +1;
+    static_assert(NX == XR_N, "register first and last passes: n_x = 256");
+    float2* line0 = reinterpret_cast<float2*>(a.psi) + (long long)l0 * NX;  // line l0 of the tile
+    {
+      const int g = tid >> 5, j = tid & 31;
+      P2 v[8];
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const float2 u0 = 2 * p < nl ? psi[(2 * p) * NX] : z;
-      const float2 u1 = 2 * p + 1 < nl ? psi[(2 * p + 1) * NX] : z;
-      p2_sts(buf, pslot<NP>(x, p), P2{make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)});
+      for (int r = 0; r < 8; ++r) {
+        const float2 u0 = 2 * g < nl ? line0[(2 * g) * NX + j + 32 * r] : z;
+        const float2 u1 = 2 * g + 1 < nl ? line0[(2 * g + 1) * NX + j + 32 * r] : z;
+        v[r] = P2{make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
+      }
+      pfirst_pass<DIR, true>(buf, v, g, j);
     }
     __syncthreads();
-    pfft_tile<NX, NP, NT, (KIND == XP_FWD ? -1 : +1), true>(buf, twb1);
-    float2 rho[NP];
+    pstockham_pass<NX, NP, NT, DIR, true, 8, 8, false, false>(buf, twb1);
+    P2 out[2][4];
+    plast_pass<DIR, true>(buf, twb1, out, tid);
+    const int j = tid & 63;
+    float2 rho[2][4];
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const P2 u = p2_lds(buf, pslot<NP>(x, p));
-      if (2 * p < nl) psi[(2 * p) * NX] = make_float2(u.re.x, u.im.x);
-      if (2 * p + 1 < nl) psi[(2 * p + 1) * NX] = make_float2(u.re.y, u.im.y);
-      rho[p] = fma2(u.re, u.re, mul2(u.im, u.im));
+    for (int it = 0; it < 2; ++it) {
+      const int g = 2 * (tid >> 6) + it;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const P2 u = out[it][r];
+        if (2 * g < nl) line0[(2 * g) * NX + j + 64 * r] = make_float2(u.re.x, u.im.x);
+        if (2 * g + 1 < nl) line0[(2 * g + 1) * NX + j + 64 * r] = make_float2(u.re.y, u.im.y);
+        rho[it][r] = fma2(u.re, u.re, mul2(u.im, u.im));
+      }
     }
     if constexpr (KIND == XP_E || KIND == XP_INV) {
       if (a.part) {  // float64 mass partial of this tile (renormalisation)
         double acc = 0.0;
 #pragma unroll
-        for (int p = 0; p < NP; ++p) acc += (double)rho[p].x + (double)rho[p].y;
+        for (int it = 0; it < 2; ++it)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) acc += (double)rho[it][r].x + (double)rho[it][r].y;
         acc = block_sum(acc, red);
         if (tid == 0) a.part[bid] = acc;
       }
     }
     if constexpr (KIND == XP_E) {
+      // the densities into the zero-padded packed tile: complex lines 2q and
+      // 2q + 1 (q = t / 64; pairs 2q, 2q + 1 of real lines) make slot q (the
+      // last pass's reads of the tile are finished before it is overwritten)
       __syncthreads();
-      r2c_rows_x2<NX>(a, buf, l0, twb2, rho);
+      const int q = tid >> 6;
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        buf[pslot<K::NP2>(j + 64 * r, q)] = make_float4(rho[0][r].x, rho[1][r].x, rho[0][r].y, rho[1][r].y);
+      r2c_rows_x2_staged<NX>(a, buf, l0, twb2);
     }
   } else {
     static_assert(KIND == XP_A, "packed x passes: X0, XI, E, A");
@@ -310,12 +369,21 @@ __device__ __forceinline__ void xpass_body_x2(const XArgs& a, const float2* __re
       p2_sts(buf, pslot<NP>(x, p), P2{yr, yi});
     }
     __syncthreads();
-    pfft_tile<NX, NP, NT, -1, true>(buf, twb1);
+    pstockham_pass<NX, NP, NT, -1, true, 8, 1, false, false>(buf, twb1);
+    pstockham_pass<NX, NP, NT, -1, true, 8, 8, false, false>(buf, twb1);
+    P2 out[2][4];
+    plast_pass<-1, true>(buf, twb1, out, tid);
+    float2* line0 = reinterpret_cast<float2*>(a.psi) + (long long)l0 * NX;
+    const int j = tid & 63;
 #pragma unroll
-    for (int p = 0; p < NP; ++p) {
-      const P2 u = p2_lds(buf, pslot<NP>(x, p));
-      if (2 * p < nl) psi[(2 * p) * NX] = make_float2(u.re.x, u.im.x);
-      if (2 * p + 1 < nl) psi[(2 * p + 1) * NX] = make_float2(u.re.y, u.im.y);
+    for (int it = 0; it < 2; ++it) {
+      const int g = 2 * (tid >> 6) + it;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const P2 u = out[it][r];
+        if (2 * g < nl) line0[(2 * g) * NX + j + 64 * r] = make_float2(u.re.x, u.im.x);
+        if (2 * g + 1 < nl) line0[(2 * g + 1) * NX + j + 64 * r] = make_float2(u.re.y, u.im.y);
+      }
     }
   }
 }
