@@ -620,7 +620,7 @@ def main():
               "gf_steps_per_s": info["outer"] / sec, "ms_per_gf_step": 1000 * sec / max(1, info["outer"]),
               "inner_iterations": info["inner"], "ms_per_inner_iteration": 1000 * sec / max(1, info["inner"]),
               "last_change": info["change"], "launches": pg.launches - lg,
-              "note": "host-timed: every BiCGStab iteration reads its inner products back"}
+              "note": "host-timed around the call; BiCGStab scalars stay on the device, each inner iteration is a replayed CUDA graph, the host polls the residual one iteration behind"}
         del pg, xg, wsg
 
     # arithmetic ceilings of this GPU, and the same step built from cuFFT

@@ -226,9 +226,7 @@ __device__ __forceinline__ void psmem_to_regs(P2 (&v)[W], const float2* buf, int
 }
 
 // Passes PASS..last of the transform of length N on v (as regs_fft, for
-// pairs). The thread index comes as an argument: a persistent caller passes a
-// value the compiler cannot see as loop-invariant, so that nothing derived from
-// it (twiddle loads, row indices) is hoisted out of the tile loop into registers.
+// pairs); tid is the thread's index in the tile.
 template <int N, int NCP, int NT, int W, int LDS, int DIR, bool EXACT, int PASS, int NS, bool REV = false,
           bool ZIN = false>
 __device__ __forceinline__ void pregs_fft(P2 (&v)[W], float2* buf, const float4* __restrict__ twb, int tid) {

@@ -771,12 +771,10 @@ __device__ __forceinline__ void colpass_tile_x2(const ColArgs& a, const MulArgs&
   x2_compute<N, VAR>(a, m, tw, g, v, tid);
 }
 
-// Persistent column pass (float pairs): block b transforms tiles b, b + G,
-// b + 2G, ... (G = gridDim.x, the blocks resident on the device). While a tile
-// is transformed, each thread's cp.async copies bring the first-pass rows of
-// its column pair of the next tile into its own staging slots, so no barrier
-// guards the staging area: a thread only ever reads the slots it filled. The
-// gathered tail tiles come first and load directly.
+// One tile of a column pass (block bid): float plans take the packed
+// column-pair path (colpass_tile_x2), float64 plans the one-column path
+// (colpass_tile). Passes over R2C bins gather the bin n_x of all planes into
+// the first tiles of the grid.
 template <typename Real, int N, int VAR>
 __device__ __forceinline__ void colpass_body(const ColArgs& a, const MulArgs& m,
                                              const typename Cplx<Real>::T* __restrict__ tw, int bid) {
@@ -985,16 +983,30 @@ __device__ __noinline__ Real lattice_integral(const XArgs& a, Real X, Real Y, Re
   return prm<Real>(a.lat_amp, a.f.lat_amp) * acc;
 }
 
+// Rounded products and fused multiply-adds that the compiler does not
+// re-associate or contract, so that every kernel that inlines an expression
+// built from them (the single-run and the batched passes) computes the same bits.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
 // P at grid point (x, y, z): the harmonic quadratic form plus, with LAT = 1,
-// the optical lattice (LAT = 2: when lat_amp != 0, decided at run time)
+// the optical lattice (LAT = 2: when lat_amp != 0, decided at run time). The
+// evaluation order is fixed: X = lo + h x, P = ((pa X X + pb Y Y) + pc X Y) + pe Z Z.
 template <typename Real, int LAT>
 __device__ __forceinline__ Real trap_phase(const XArgs& a, int x, int y, int z) {
-  const Real X = prm<Real>(a.lo0, a.f.lo0) + prm<Real>(a.h0, a.f.h0) * Real(x);
-  const Real Y = prm<Real>(a.lo1, a.f.lo1) + prm<Real>(a.h1, a.f.h1) * Real(y);
-  const Real Z = prm<Real>(a.lo2, a.f.lo2) + prm<Real>(a.h2, a.f.h2) * Real(z);
-  const Real P = prm<Real>(a.pa, a.f.pa) * X * X + prm<Real>(a.pb, a.f.pb) * Y * Y +
-                 prm<Real>(a.pc, a.f.pc) * X * Y + prm<Real>(a.pe, a.f.pe) * Z * Z;
-  if (LAT == 1 || (LAT == 2 && prm<Real>(a.lat_amp, a.f.lat_amp) != Real(0))) return P + lattice_integral<Real>(a, X, Y, Z);
+  const Real X = fma_rn(prm<Real>(a.h0, a.f.h0), Real(x), prm<Real>(a.lo0, a.f.lo0));
+  const Real Y = fma_rn(prm<Real>(a.h1, a.f.h1), Real(y), prm<Real>(a.lo1, a.f.lo1));
+  const Real Z = fma_rn(prm<Real>(a.h2, a.f.h2), Real(z), prm<Real>(a.lo2, a.f.lo2));
+  Real P = mul_rn(mul_rn(prm<Real>(a.pa, a.f.pa), X), X);
+  P = fma_rn(mul_rn(prm<Real>(a.pb, a.f.pb), Y), Y, P);
+  P = fma_rn(mul_rn(prm<Real>(a.pc, a.f.pc), X), Y, P);
+  P = fma_rn(mul_rn(prm<Real>(a.pe, a.f.pe), Z), Z, P);
+  if (LAT == 1 || (LAT == 2 && prm<Real>(a.lat_amp, a.f.lat_amp) != Real(0)))
+    return add_rn(P, lattice_integral<Real>(a, X, Y, Z));
   return P;
 }
 

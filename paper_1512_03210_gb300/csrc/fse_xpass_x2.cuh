@@ -20,11 +20,15 @@
 // radix-8 pass fall on different bank halves) and slot p sits at column
 // p ^ ((j >> 1) & 3).
 //
-// Each thread owns one position x of the 256-point lines (x = thread index)
-// and all 8 pairs there. Used for the float passes X0 (forward x), XI (inverse
-// x), E (inverse x, density, zero-padded R2C) and A (cropped C2R, potential
-// phase, forward x) at n_x = 256 with 16-line tiles; other passes and sizes
-// run the one-line code (xpass_body).
+// The transforms of the lines (plan 8, 8, 4) load their first pass from
+// global memory and keep their last pass in registers, stored straight back,
+// so that the tile is exchanged through shared memory once; pass E's densities
+// enter the first pass of the zero-padded R2C in registers too. The potential
+// phase of pass A is computed with one position x per thread (all 8 pairs),
+// the layout the C2R leaves in shared memory. Used for the float passes X0
+// (forward x), XI (inverse x), E (inverse x, density, zero-padded R2C) and A
+// (cropped C2R, potential phase, forward x) at n_x = 256 with 16-line tiles of
+// 256 threads; other passes and sizes run the one-line code (xpass_body).
 #pragma once
 
 #include "fse_fft_x2.cuh"
@@ -34,7 +38,7 @@ namespace fse {
 template <int NX>
 struct XCfg2 {
   static constexpr int NCOL = 16, NP = 8, NP2 = 4, NT = 256;
-  static_assert(NX == NT, "one position per thread");
+  static_assert(NX == NT, "one position per thread in pass A's phase");
   static constexpr int PERP = NP;            // pairs per thread (all pairs at position x)
   static constexpr int NH = NP2 * (NX + 1);  // (complex-line pair, bin) items of the half spectrum
   static constexpr int PH = (NH + NT - 1) / NT;
@@ -139,13 +143,16 @@ __device__ __forceinline__ void pfirst_pass(float4* buf, P2 (&v)[8], int g, int 
 }
 
 // Last pass (radix 4, twiddles j r) from the tile into registers: out[it][r]
-// holds position j + 64 r of pair g_it = 2 (t / 64) + it (j = t % 64).
-template <int DIR, bool EXACT>
+// holds position j + 64 r of pair g_it = 2 p + it, with p = t / 64, j = t % 64
+// (SLOT false: a warp stores 256 contiguous bytes of a line), or p = t % 4,
+// j = t / 4 (SLOT true: the two pairs of a thread are slot p of the
+// zero-padded density tile at the rows its first radix-8 pass reads).
+template <int DIR, bool EXACT, bool SLOT = false>
 __device__ __forceinline__ void plast_pass(const float4* buf, const float4* __restrict__ twb, P2 (&out)[2][4], int tid) {
-  const int j = tid & 63;
+  const int j = SLOT ? tid >> 2 : tid & 63;
 #pragma unroll
   for (int it = 0; it < 2; ++it) {
-    const int g = 2 * (tid >> 6) + it;
+    const int g = 2 * (SLOT ? tid & 3 : tid >> 6) + it;
 #pragma unroll
     for (int r = 0; r < 4; ++r) out[it][r] = p2_lds(buf, pslot<8>(j + 64 * r, g));
 #pragma unroll
@@ -159,17 +166,34 @@ __device__ __forceinline__ void plast_pass(const float4* buf, const float4* __re
 // part), two complex lines one slot; one packed FFT of length 2 NX; the
 // spectra are separated with A_k = (Z_k + conj Z_-k)/2, B_k = (Z_k - conj
 // Z_-k)/(2i). Ends without a barrier.
-// The caller has written the densities into rows 0..NX-1 of the packed tile
-// (complex line c in lane c & 1 of slot c >> 1) and not synchronised.
+// Thread t holds the densities rho[it][r] of pair 2 (t % 4) + it at positions
+// t / 4 + 64 r (plast_pass with SLOT): the lines of slot q = t % 4 at the rows
+// item t / 4 of the first radix-8 pass reads (rows NX..2NX-1 are the zero
+// padding and are not read), so that pass runs on registers. The caller has
+// synchronised (buf free).
 template <int NX>
-__device__ __forceinline__ void r2c_rows_x2_staged(const XArgs& a, float4* buf, int l0,
-                                                   const float4* __restrict__ twb2) {
+__device__ __forceinline__ void r2c_rows_x2(const XArgs& a, float4* buf, int l0, const float4* __restrict__ twb2,
+                                            const float2 (&rho)[2][4]) {
   typedef XCfg2<NX> K;
   constexpr int NP2 = K::NP2, NT = K::NT;
+  static_assert(2 * NX == 512 && radix_plan(2 * NX).npass == 3 && radix_plan(2 * NX).r[0] == 8,
+                "R2C with its first pass on registers: length 512, plan 8, 8, 8");
   const int tid = threadIdx.x;
-  // rows NX..2NX-1 are the zero padding: the first (radix-8) pass does not read them
+  {
+    const int q = tid & 3, j = tid >> 2;
+    P2 v[8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      v[r] = P2{make_float2(rho[0][r].x, rho[1][r].x), make_float2(rho[0][r].y, rho[1][r].y)};
+      v[r + 4] = P2{bc(0.f), bc(0.f)};
+    }
+    pdft<8, -1, false, true>(v);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) p2_sts(buf, pslot<NP2>(8 * j + r, q), v[r]);
+  }
   __syncthreads();
-  pfft_tile<2 * NX, NP2, NT, -1, false, true, false>(buf, twb2);
+  pstockham_pass<2 * NX, NP2, NT, -1, false, 8, 8, false, false>(buf, twb2);
+  pstockham_pass<2 * NX, NP2, NT, -1, false, 8, 64, false, false>(buf, twb2);
   float2* S = reinterpret_cast<float2*>(a.spec);
   const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
   const float2 half = bc(0.5f);
@@ -286,13 +310,14 @@ __device__ __forceinline__ void xpass_body_x2(const XArgs& a, const float2* __re
     }
     __syncthreads();
     pstockham_pass<NX, NP, NT, DIR, true, 8, 8, false, false>(buf, twb1);
+    constexpr bool SLOT = KIND == XP_E;
     P2 out[2][4];
-    plast_pass<DIR, true>(buf, twb1, out, tid);
-    const int j = tid & 63;
+    plast_pass<DIR, true, SLOT>(buf, twb1, out, tid);
+    const int j = SLOT ? tid >> 2 : tid & 63;
     float2 rho[2][4];
 #pragma unroll
     for (int it = 0; it < 2; ++it) {
-      const int g = 2 * (tid >> 6) + it;
+      const int g = 2 * (SLOT ? tid & 3 : tid >> 6) + it;
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const P2 u = out[it][r];
@@ -313,15 +338,9 @@ __device__ __forceinline__ void xpass_body_x2(const XArgs& a, const float2* __re
       }
     }
     if constexpr (KIND == XP_E) {
-      // the densities into the zero-padded packed tile: complex lines 2q and
-      // 2q + 1 (q = t / 64; pairs 2q, 2q + 1 of real lines) make slot q (the
-      // last pass's reads of the tile are finished before it is overwritten)
+      // the last pass's reads of the tile are finished before it is overwritten
       __syncthreads();
-      const int q = tid >> 6;
-#pragma unroll
-      for (int r = 0; r < 4; ++r)
-        buf[pslot<K::NP2>(j + 64 * r, q)] = make_float4(rho[0][r].x, rho[1][r].x, rho[0][r].y, rho[1][r].y);
-      r2c_rows_x2_staged<NX>(a, buf, l0, twb2);
+      r2c_rows_x2<NX>(a, buf, l0, twb2, rho);
     }
   } else {
     static_assert(KIND == XP_A, "packed x passes: X0, XI, E, A");
