@@ -40,8 +40,9 @@ struct XCfg2 {
   static constexpr int NCOL = 16, NP = 8, NP2 = 4, NT = 256;
   static_assert(NX == NT, "one position per thread in pass A's phase");
   static constexpr int PERP = NP;            // pairs per thread (all pairs at position x)
-  static constexpr int NH = NP2 * (NX + 1);  // (complex-line pair, bin) items of the half spectrum
-  static constexpr int PH = (NH + NT - 1) / NT;
+  static constexpr int NB = NX / 2 + 1;      // bin pairs (2b, 2b + 1) of a half spectrum (bins 0..NX)
+  static constexpr int NHB = NP2 * NB;       // (complex-line pair, bin pair) items
+  static constexpr int PHB = (NHB + NT - 1) / NT;
 };
 
 template <int NX> __host__ __device__ constexpr bool xpass_x2_ok() {
@@ -197,22 +198,37 @@ __device__ __forceinline__ void r2c_rows_x2(const XArgs& a, float4* buf, int l0,
   float2* S = reinterpret_cast<float2*>(a.spec);
   const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
   const float2 half = bc(0.5f);
+  // bins in pairs (2b, 2b + 1), one 16-byte store per line (rows of S are
+  // 16-byte aligned); the last pair is bin NX alone
 #pragma unroll
-  for (int it = 0; it < K::PH; ++it) {
+  for (int it = 0; it < K::PHB; ++it) {
     const int idx = tid + it * NT;
-    if (idx < K::NH) {
-      const int q = idx / (NX + 1), k = idx % (NX + 1);
-      const P2 zk = p2_lds(buf, pslot<NP2>(k, q));
-      const P2 zm = p2_lds(buf, pslot<NP2>((2 * NX - k) % (2 * NX), q));
-      const float2 ar = mul2(half, add2(zk.re, zm.re)), ai = mul2(half, sub2(zk.im, zm.im));
-      const float2 br = mul2(half, add2(zk.im, zm.im)), bi = mul2(half, sub2(zm.re, zk.re));
-      // complex line 2q + c carries real lines 4q + 2c (A) and 4q + 2c + 1 (B)
-      const int lb = 4 * q;
-      const float2 vals[4] = {make_float2(ar.x, ai.x), make_float2(br.x, bi.x), make_float2(ar.y, ai.y),
-                              make_float2(br.y, bi.y)};
+    if (idx < K::NHB) {
+      const int q = idx / K::NB, k0 = 2 * (idx % K::NB);
+      float2 vals[2][4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (l0 + lb + u < a.nlines) S[srow(y0, z0, lb + u, a.ny, a.srow_mul) * a.sx + k] = vals[u];
+      for (int h = 0; h < 2; ++h) {
+        const int k = min(k0 + h, NX);
+        const P2 zk = p2_lds(buf, pslot<NP2>(k, q));
+        const P2 zm = p2_lds(buf, pslot<NP2>((2 * NX - k) % (2 * NX), q));
+        const float2 ar = mul2(half, add2(zk.re, zm.re)), ai = mul2(half, sub2(zk.im, zm.im));
+        const float2 br = mul2(half, add2(zk.im, zm.im)), bi = mul2(half, sub2(zm.re, zk.re));
+        // complex line 2q + c carries real lines 4q + 2c (A) and 4q + 2c + 1 (B)
+        vals[h][0] = make_float2(ar.x, ai.x);
+        vals[h][1] = make_float2(br.x, bi.x);
+        vals[h][2] = make_float2(ar.y, ai.y);
+        vals[h][3] = make_float2(br.y, bi.y);
+      }
+      const int lb = 4 * q;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (l0 + lb + u >= a.nlines) continue;
+        float2* row = &S[srow(y0, z0, lb + u, a.ny, a.srow_mul) * a.sx + k0];
+        if (k0 < NX)
+          *reinterpret_cast<float4*>(row) = make_float4(vals[0][u].x, vals[0][u].y, vals[1][u].x, vals[1][u].y);
+        else
+          *row = vals[0][u];
+      }
     }
   }
 }
@@ -230,22 +246,35 @@ __device__ __forceinline__ void c2r_rows_x2(const XArgs& a, float4* buf, int l0,
   const int tid = threadIdx.x, x = tid;
   const float2* S = reinterpret_cast<const float2*>(a.spec);
   const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
+  // bins in pairs (2b, 2b + 1), one 16-byte load per line (rows of S are
+  // 16-byte aligned: sx is a multiple of 16); the last pair holds bin NX and a
+  // padding bin of the row, which is not used
 #pragma unroll
-  for (int it = 0; it < K::PH; ++it) {
+  for (int it = 0; it < K::PHB; ++it) {
     const int idx = tid + it * NT;
-    if (idx < K::NH) {
-      const int q = idx / (NX + 1), k = idx % (NX + 1);
+    if (idx < K::NHB) {
+      const int q = idx / K::NB, k0 = 2 * (idx % K::NB);
       const int lb = 4 * q;
-      float2 v[4];
+      float4 v[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        v[u] = (l0 + lb + u < a.nlines) ? S[srow(y0, z0, lb + u, a.ny, a.srow_mul) * a.sx + k] : make_float2(0.f, 0.f);
-      // lane c: A = v[2c], B = v[2c + 1]; Z_k = A + i B, Z_{2NX-k} = conj(A) + i conj(B)
-      const P2 zk{make_float2(v[0].x - v[1].y, v[2].x - v[3].y), make_float2(v[0].y + v[1].x, v[2].y + v[3].x)};
-      p2_sts(buf, pslot<NP2>(k, q), zk);
-      if (k > 0 && k < NX) {
-        const P2 zm{make_float2(v[0].x + v[1].y, v[2].x + v[3].y), make_float2(v[1].x - v[0].y, v[3].x - v[2].y)};
-        p2_sts(buf, pslot<NP2>(2 * NX - k, q), zm);
+        v[u] = (l0 + lb + u < a.nlines)
+                   ? *reinterpret_cast<const float4*>(&S[srow(y0, z0, lb + u, a.ny, a.srow_mul) * a.sx + k0])
+                   : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = k0 + h;
+        if (k > NX) break;
+        float2 w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = h ? make_float2(v[u].z, v[u].w) : make_float2(v[u].x, v[u].y);
+        // lane c: A = w[2c], B = w[2c + 1]; Z_k = A + i B, Z_{2NX-k} = conj(A) + i conj(B)
+        const P2 zk{make_float2(w[0].x - w[1].y, w[2].x - w[3].y), make_float2(w[0].y + w[1].x, w[2].y + w[3].x)};
+        p2_sts(buf, pslot<NP2>(k, q), zk);
+        if (k > 0 && k < NX) {
+          const P2 zm{make_float2(w[0].x + w[1].y, w[2].x + w[3].y), make_float2(w[1].x - w[0].y, w[3].x - w[2].y)};
+          p2_sts(buf, pslot<NP2>(2 * NX - k, q), zm);
+        }
       }
     }
   }
