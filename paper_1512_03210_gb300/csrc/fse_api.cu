@@ -461,7 +461,8 @@ fse_status run_steps(fse_plan* P, void* psi, double t0, int nsteps, const double
   XArgs xa = x_args(P, psi, nl ? spec : nullptr);
   XArgs xe = xa;  // E or XI: also writes the mass partials when renormalising
   if (rn) xe.part = renorm_part(P);
-  const int ncx = P->prec == FSE_F32 ? xpass_ncol<float>(P->nx) : xpass_ncol<double>(P->nx);
+  // tiles of pass E, one mass partial each
+  const int ncx = P->prec == FSE_F32 ? xpass_ncol_x2<float>(P->nx) : xpass_ncol_x2<double>(P->nx);
   const int xblocks = (xa.nlines + ncx - 1) / ncx;
   // sub-steps of one step: TS2-GauSum itself, or the fourth-order triple jump
   // w1, w0, w1; the kinetic half steps between sub-steps and between steps merge

@@ -54,7 +54,7 @@ k_colpass_batch(ColArgs a, MulArgs m, const typename Cplx<Real>::T* __restrict__
 }
 
 template <typename Real, int NX, int KIND>
-__global__ void __launch_bounds__(XCfg<Real, NX>::NT, XCfg<Real, NX>::MINB)
+__global__ void __launch_bounds__(XLaunch<Real, NX, KIND>::NT, XLaunch<Real, NX, KIND>::MINB)
 k_xpass_batch(XArgs a, const typename Cplx<Real>::T* __restrict__ twn, const typename Cplx<Real>::T* __restrict__ tw2n,
               const BatchRun* runs, const double* t0p, int step) {
   const BatchRun r = runs[blockIdx.y];
@@ -111,7 +111,7 @@ static cudaError_t launch_colb(int N, int mode, const ColArgs& a, const MulArgs&
 template <int NX, int KIND>
 static cudaError_t xb(const XArgs& a, const void* twn, const void* tw2n, const BatchRun* runs, int nr,
                       const double* t0, int step, cudaStream_t st) {
-  typedef XCfg<float, NX> K;
+  typedef XLaunch<float, NX, KIND> K;
   const size_t smem = K::smem_bytes();
   static std::atomic<unsigned long long> done{0};
   cudaError_t e = allow_smem(k_xpass_batch<float, NX, KIND>, smem, done);

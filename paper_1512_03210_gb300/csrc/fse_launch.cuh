@@ -86,8 +86,8 @@ template <typename Real> int colpass_ncol(int N) {
 
 template <typename Real, int NX, int KIND>
 static cudaError_t x_launch(const XArgs& a, const void* twn, const void* tw2n, cudaStream_t st) {
-  typedef XCfg<Real, NX> K;
-  typedef typename K::C C;
+  typedef XLaunch<Real, NX, KIND> K;
+  typedef typename Cplx<Real>::T C;
   const size_t smem = K::smem_bytes();
   static std::atomic<unsigned long long> done{0};
   cudaError_t e = allow_smem(k_xpass<Real, NX, KIND>, smem, done);
@@ -128,6 +128,18 @@ template <typename Real> int xpass_ncol(int nx) {
 #define FSE_CASE(n) \
   case n:           \
     return XCfg<Real, n>::NCOL;
+    FSE_X_SIZES(FSE_CASE)
+#undef FSE_CASE
+    default:
+      return 0;
+  }
+}
+
+template <typename Real> int xpass_ncol_x2(int nx) {
+  switch (nx) {
+#define FSE_CASE(n) \
+  case n:           \
+    return XLaunch<Real, n, XP_E>::NCOL;
     FSE_X_SIZES(FSE_CASE)
 #undef FSE_CASE
     default:

@@ -1231,20 +1231,35 @@ __device__ __forceinline__ void xpass_body(const XArgs& a, const typename Cplx<R
 
 namespace fse {
 
-// An x pass: the packed two-line code where it applies (fse_xpass_x2.cuh),
-// the one-line code otherwise.
+// Whether an x pass takes the packed two-line code (fse_xpass_x2.cuh), and
+// the launch shape of either code: lines per tile, threads, resident tiles
+// per SM the registers are sized for, dynamic shared memory.
+template <typename Real, int NX, int KIND>
+struct XLaunch {
+  static constexpr bool X2 = sizeof(Real) == 4 && xpass_x2_ok<NX>() &&
+                             (KIND == XP_FWD || KIND == XP_INV || KIND == XP_E || KIND == XP_A);
+  static constexpr int NCOL = X2 ? XCfg2<(X2 ? NX : 256)>::NCOL : XCfg<Real, NX>::NCOL;
+  static constexpr int NT = X2 ? XCfg2<(X2 ? NX : 256)>::NT : XCfg<Real, NX>::NT;
+  static constexpr int MINB = X2 ? XCfg2<(X2 ? NX : 256)>::MINB : XCfg<Real, NX>::MINB;
+  __host__ __device__ static constexpr size_t smem_bytes() {
+    return X2 && XCfg2<(X2 ? NX : 256)>::SMEM > XCfg<Real, NX>::smem_bytes() ? XCfg2<(X2 ? NX : 256)>::SMEM
+                                                                              : XCfg<Real, NX>::smem_bytes();
+  }
+};
+
+// An x pass: the packed two-line code where it applies, the one-line code
+// otherwise.
 template <typename Real, int NX, int KIND>
 __device__ __forceinline__ void xpass_any(const XArgs& a, const typename Cplx<Real>::T* __restrict__ twn,
                                           const typename Cplx<Real>::T* __restrict__ tw2n, int bid) {
-  if constexpr (sizeof(Real) == 4 && xpass_x2_ok<NX>() &&
-                (KIND == XP_FWD || KIND == XP_INV || KIND == XP_E || KIND == XP_A))
+  if constexpr (XLaunch<Real, NX, KIND>::X2)
     xpass_body_x2<NX, KIND>(a, twn, tw2n, bid);
   else
     xpass_body<Real, NX, KIND>(a, twn, tw2n, bid);
 }
 
 template <typename Real, int NX, int KIND>
-__global__ void __launch_bounds__(XCfg<Real, NX>::NT, XCfg<Real, NX>::MINB)
+__global__ void __launch_bounds__(XLaunch<Real, NX, KIND>::NT, XLaunch<Real, NX, KIND>::MINB)
 k_xpass(XArgs a, const typename Cplx<Real>::T* __restrict__ twn, const typename Cplx<Real>::T* __restrict__ tw2n) {
   pass_prologue();
   xpass_any<Real, NX, KIND>(a, twn, tw2n, blockIdx.x);
@@ -1256,8 +1271,11 @@ cudaError_t launch_colpass(int N, int var, const ColArgs& a, const MulArgs& m, c
 template <typename Real>
 cudaError_t launch_xpass(int kind, int nx, const XArgs& a, const void* twn, const void* tw2n,
                          cudaStream_t st);
-// Lines per tile of the column pass of length N and of the x passes of length nx.
+// Lines per tile of the column pass of length N and of the x passes of length
+// nx (xpass_ncol: the one-line kinds; xpass_ncol_x2: the kinds X0, XI, E and
+// A, which write the renormalisation partials of XI and E per tile).
 template <typename Real> int colpass_ncol(int N);
 template <typename Real> int xpass_ncol(int nx);
+template <typename Real> int xpass_ncol_x2(int nx);
 
 }  // namespace fse

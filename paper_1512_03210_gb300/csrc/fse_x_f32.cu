@@ -4,4 +4,5 @@
 namespace fse {
 template cudaError_t launch_xpass<float>(int, int, const XArgs&, const void*, const void*, cudaStream_t);
 template int xpass_ncol<float>(int);
+template int xpass_ncol_x2<float>(int);
 }  // namespace fse

@@ -4,4 +4,5 @@
 namespace fse {
 template cudaError_t launch_xpass<double>(int, int, const XArgs&, const void*, const void*, cudaStream_t);
 template int xpass_ncol<double>(int);
+template int xpass_ncol_x2<double>(int);
 }  // namespace fse

@@ -20,34 +20,39 @@
 // radix-8 pass fall on different bank halves) and slot p sits at column
 // p ^ ((j >> 1) & 3).
 //
-// The transforms of the lines (plan 8, 8, 4) load their first pass from
+// The transforms of the lines (plan 8, 8, 4 or 8, 8, 8) load their first pass from
 // global memory and keep their last pass in registers, stored straight back,
 // so that the tile is exchanged through shared memory once; pass E's densities
 // enter the first pass of the zero-padded R2C in registers too. The potential
 // phase of pass A is computed with one position x per thread (all 8 pairs),
 // the layout the C2R leaves in shared memory. Used for the float passes X0
 // (forward x), XI (inverse x), E (inverse x, density, zero-padded R2C) and A
-// (cropped C2R, potential phase, forward x) at n_x = 256 with 16-line tiles of
-// 256 threads; other passes and sizes run the one-line code (xpass_body).
+// (cropped C2R, potential phase, forward x) at n_x = 256 and 512 with 16-line
+// tiles of n_x threads; other passes and sizes run the one-line code
+// (xpass_body). At n_x = 512 the densities reach the R2C through the tile.
 #pragma once
 
 #include "fse_fft_x2.cuh"
 
 namespace fse {
 
+template <int NX> __host__ __device__ constexpr bool xpass_x2_ok() { return NX == 256 || NX == 512; }
+
+// A tile is 16 lines and NX threads (one position per thread in pass A's
+// phase): at n_x = 256 four tiles of 32 KB per SM, at n_x = 512 two of 64 KB.
 template <int NX>
 struct XCfg2 {
-  static constexpr int NCOL = 16, NP = 8, NP2 = 4, NT = 256;
-  static_assert(NX == NT, "one position per thread in pass A's phase");
+  static_assert(xpass_x2_ok<NX>(), "packed x passes: n_x = 256 or 512");
+  static constexpr int NCOL = 16, NP = 8, NP2 = 4, NT = NX;
+  static constexpr int MINB = 1024 / NT;     // 64 registers per thread
   static constexpr int PERP = NP;            // pairs per thread (all pairs at position x)
   static constexpr int NB = NX / 2 + 1;      // bin pairs (2b, 2b + 1) of a half spectrum (bins 0..NX)
   static constexpr int NHB = NP2 * NB;       // (complex-line pair, bin pair) items
   static constexpr int PHB = (NHB + NT - 1) / NT;
+  // the 8-slot tile of the lines (NX rows) and the 4-slot tile of the
+  // zero-padded densities (2 NX rows) share the buffer
+  static constexpr size_t SMEM = 16 * (size_t)NX * NP;
 };
-
-template <int NX> __host__ __device__ constexpr bool xpass_x2_ok() {
-  return NX == 256 && ncol_for(2 * NX, 8) == 16;
-}
 
 // slot of (row, pair) in a tile of NP = 8 or NP = 4 slots per row (see above)
 template <int NP> __device__ __forceinline__ int pslot(int row, int p) {
@@ -123,19 +128,20 @@ __device__ __forceinline__ void pfft_tile(float4* buf, const float4* __restrict_
   pstockham_rec<N, NP, NT, DIR, EXACT, 0, 1, ZIN, ZOUT>(buf, twb);
 }
 
-// The length-256 transforms of the lines (plan 8, 8, 4) with their first
-// pass on registers and their last pass into registers, so that the tile is
-// read from and written to global memory directly: thread t works on pair
+// The transforms of the lines with their first pass on registers and their
+// last pass into registers, so that the tile is read from and written to
+// global memory directly. Length 256 (plan 8, 8, 4): thread t works on pair
 // g = t / 32 and positions j + 32 r (first pass, j = t % 32), and on pairs
-// 2 (t / 64) and 2 (t / 64) + 1 at positions j + 64 r (last pass, j = t % 64),
-// both coalesced along the lines.
-constexpr int XR_N = 256;
-static_assert(radix_plan(XR_N).npass == 3 && radix_plan(XR_N).r[0] == 8 && radix_plan(XR_N).r[1] == 8 &&
-                  radix_plan(XR_N).r[2] == 4,
-              "register first and last passes: plan 8, 8, 4");
+// 2 (t / 64) and 2 (t / 64) + 1 at positions j + 64 r (last pass, j = t % 64).
+// Length 512 (plan 8, 8, 8): pair t / 64 and positions t % 64 + 64 r in both.
+// Both coalesced along the lines.
+static_assert(radix_plan(256).npass == 3 && radix_plan(256).r[0] == 8 && radix_plan(256).r[1] == 8 &&
+                  radix_plan(256).r[2] == 4 && radix_plan(512).npass == 3 && radix_plan(512).r[0] == 8 &&
+                  radix_plan(512).r[1] == 8 && radix_plan(512).r[2] == 8,
+              "register first and last passes: plans 8, 8, 4 and 8, 8, 8");
 
-// First pass (radix 8, no twiddles) of the values v[r] at positions j + 32 r
-// of pair g, written to the tile (the caller synchronises after).
+// First pass (radix 8, no twiddles) of the values v[r] at positions
+// j + (NX / 8) r of pair g, written to the tile (the caller synchronises after).
 template <int DIR, bool EXACT>
 __device__ __forceinline__ void pfirst_pass(float4* buf, P2 (&v)[8], int g, int j) {
   pdft<8, DIR, EXACT, false>(v);
@@ -162,39 +168,25 @@ __device__ __forceinline__ void plast_pass(const float4* buf, const float4* __re
   }
 }
 
-// Densities of the tile's lines -> x-half-spectra of the zero-padded lines in
-// S. Two real lines form one complex line (line 2p real part, 2p + 1 imaginary
-// part), two complex lines one slot; one packed FFT of length 2 NX; the
-// spectra are separated with A_k = (Z_k + conj Z_-k)/2, B_k = (Z_k - conj
-// Z_-k)/(2i). Ends without a barrier.
-// Thread t holds the densities rho[it][r] of pair 2 (t % 4) + it at positions
-// t / 4 + 64 r (plast_pass with SLOT): the lines of slot q = t % 4 at the rows
-// item t / 4 of the first radix-8 pass reads (rows NX..2NX-1 are the zero
-// padding and are not read), so that pass runs on registers. The caller has
-// synchronised (buf free).
+// Last pass (radix R, stride N / R) of pair g of the 8-slot tile, item j,
+// into registers: v[r] = output position j + (N / R) r.
+template <int N, int R, int DIR, bool EXACT>
+__device__ __forceinline__ void preg_last(const float4* buf, const float4* __restrict__ twb, P2 (&v)[R], int g, int j) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) v[r] = p2_lds(buf, pslot<8>(j + (N / R) * r, g));
+#pragma unroll
+  for (int r = 1; r < R; ++r) v[r] = ptwiddle<DIR, EXACT>(v[r], twb, j * r);
+  pdft<R, DIR, EXACT, false>(v);
+}
+
+// The transformed densities in the packed tile (Z_k of complex line 2q + c in
+// lane c of slot q, row k; the caller's last pass ended with a barrier) ->
+// x-half-spectra of the tile's lines in S. Ends without a barrier.
 template <int NX>
-__device__ __forceinline__ void r2c_rows_x2(const XArgs& a, float4* buf, int l0, const float4* __restrict__ twb2,
-                                            const float2 (&rho)[2][4]) {
+__device__ __forceinline__ void r2c_separate(const XArgs& a, const float4* buf, int l0) {
   typedef XCfg2<NX> K;
   constexpr int NP2 = K::NP2, NT = K::NT;
-  static_assert(2 * NX == 512 && radix_plan(2 * NX).npass == 3 && radix_plan(2 * NX).r[0] == 8,
-                "R2C with its first pass on registers: length 512, plan 8, 8, 8");
   const int tid = threadIdx.x;
-  {
-    const int q = tid & 3, j = tid >> 2;
-    P2 v[8];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      v[r] = P2{make_float2(rho[0][r].x, rho[1][r].x), make_float2(rho[0][r].y, rho[1][r].y)};
-      v[r + 4] = P2{bc(0.f), bc(0.f)};
-    }
-    pdft<8, -1, false, true>(v);
-#pragma unroll
-    for (int r = 0; r < 8; ++r) p2_sts(buf, pslot<NP2>(8 * j + r, q), v[r]);
-  }
-  __syncthreads();
-  pstockham_pass<2 * NX, NP2, NT, -1, false, 8, 8, false, false>(buf, twb2);
-  pstockham_pass<2 * NX, NP2, NT, -1, false, 8, 64, false, false>(buf, twb2);
   float2* S = reinterpret_cast<float2*>(a.spec);
   const int z0 = l0 / a.ny, y0 = l0 - z0 * a.ny;
   const float2 half = bc(0.5f);
@@ -231,6 +223,54 @@ __device__ __forceinline__ void r2c_rows_x2(const XArgs& a, float4* buf, int l0,
       }
     }
   }
+}
+
+// Densities of the tile's lines -> x-half-spectra of the zero-padded lines in
+// S. Two real lines form one complex line (line 2p real part, 2p + 1 imaginary
+// part), two complex lines one slot; one packed FFT of length 2 NX; the
+// spectra are separated with A_k = (Z_k + conj Z_-k)/2, B_k = (Z_k - conj
+// Z_-k)/(2i). Ends without a barrier.
+// Thread t holds the densities rho[it][r] of pair 2 (t % 4) + it at positions
+// t / 4 + 64 r (plast_pass with SLOT): the lines of slot q = t % 4 at the rows
+// item t / 4 of the first radix-8 pass reads (rows NX..2NX-1 are the zero
+// padding and are not read), so that pass runs on registers. The caller has
+// synchronised (buf free).
+template <int NX>
+__device__ __forceinline__ void r2c_rows_x2(const XArgs& a, float4* buf, int l0, const float4* __restrict__ twb2,
+                                            const float2 (&rho)[2][4]) {
+  typedef XCfg2<NX> K;
+  constexpr int NP2 = K::NP2, NT = K::NT;
+  static_assert(2 * NX == 512 && radix_plan(2 * NX).npass == 3 && radix_plan(2 * NX).r[0] == 8,
+                "R2C with its first pass on registers: length 512, plan 8, 8, 8");
+  const int tid = threadIdx.x;
+  {
+    const int q = tid & 3, j = tid >> 2;
+    P2 v[8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      v[r] = P2{make_float2(rho[0][r].x, rho[1][r].x), make_float2(rho[0][r].y, rho[1][r].y)};
+      v[r + 4] = P2{bc(0.f), bc(0.f)};
+    }
+    pdft<8, -1, false, true>(v);
+#pragma unroll
+    for (int r = 0; r < 8; ++r) p2_sts(buf, pslot<NP2>(8 * j + r, q), v[r]);
+  }
+  __syncthreads();
+  pstockham_pass<2 * NX, NP2, NT, -1, false, 8, 8, false, false>(buf, twb2);
+  pstockham_pass<2 * NX, NP2, NT, -1, false, 8, 64, false, false>(buf, twb2);
+  r2c_separate<NX>(a, buf, l0);
+}
+
+// The densities written into rows 0..NX-1 of the packed tile (complex line c
+// in lane c & 1 of slot c >> 1; the caller has not synchronised) -> S, as
+// r2c_rows_x2 with the whole transform in shared memory.
+template <int NX>
+__device__ __forceinline__ void r2c_rows_staged(const XArgs& a, float4* buf, int l0, const float4* __restrict__ twb2) {
+  typedef XCfg2<NX> K;
+  // rows NX..2NX-1 are the zero padding: the first (radix-8) pass does not read them
+  __syncthreads();
+  pfft_tile<2 * NX, K::NP2, K::NT, -1, false, true, false>(buf, twb2);
+  r2c_separate<NX>(a, buf, l0);
 }
 
 // x-half-spectra in S of the tile's lines -> real values val[p] of lines 2p,
@@ -324,52 +364,90 @@ __device__ __forceinline__ void xpass_body_x2(const XArgs& a, const float2* __re
 
   if constexpr (KIND == XP_FWD || KIND == XP_INV || KIND == XP_E) {
     constexpr int DIR = KIND == XP_FWD ? -1 : +1;
-    static_assert(NX == XR_N, "register first and last passes: n_x = 256");
+    constexpr int L = NX / 8;  // first pass: pair t / L, positions t % L + L r
     float2* line0 = reinterpret_cast<float2*>(a.psi) + (long long)l0 * NX;  // line l0 of the tile
     {
-      const int g = tid >> 5, j = tid & 31;
+      const int g = tid / L, j = tid % L;
       P2 v[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        const float2 u0 = 2 * g < nl ? line0[(2 * g) * NX + j + 32 * r] : z;
-        const float2 u1 = 2 * g + 1 < nl ? line0[(2 * g + 1) * NX + j + 32 * r] : z;
+        const float2 u0 = 2 * g < nl ? line0[(2 * g) * NX + j + L * r] : z;
+        const float2 u1 = 2 * g + 1 < nl ? line0[(2 * g + 1) * NX + j + L * r] : z;
         v[r] = P2{make_float2(u0.x, u1.x), make_float2(u0.y, u1.y)};
       }
       pfirst_pass<DIR, true>(buf, v, g, j);
     }
     __syncthreads();
     pstockham_pass<NX, NP, NT, DIR, true, 8, 8, false, false>(buf, twb1);
-    constexpr bool SLOT = KIND == XP_E;
-    P2 out[2][4];
-    plast_pass<DIR, true, SLOT>(buf, twb1, out, tid);
-    const int j = SLOT ? tid >> 2 : tid & 63;
-    float2 rho[2][4];
+    if constexpr (NX == 512) {
+      // last pass (radix 8, stride 64): pair t / 64, positions t % 64 + 64 r
+      const int g = tid >> 6, j = tid & 63;
+      P2 out[8];
+      preg_last<NX, 8, DIR, true>(buf, twb1, out, g, j);
+      float2 rho[8];
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const int g = 2 * (SLOT ? tid & 3 : tid >> 6) + it;
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const P2 u = out[it][r];
+      for (int r = 0; r < 8; ++r) {
+        const P2 u = out[r];
         if (2 * g < nl) line0[(2 * g) * NX + j + 64 * r] = make_float2(u.re.x, u.im.x);
         if (2 * g + 1 < nl) line0[(2 * g + 1) * NX + j + 64 * r] = make_float2(u.re.y, u.im.y);
-        rho[it][r] = fma2(u.re, u.re, mul2(u.im, u.im));
+        rho[r] = fma2(u.re, u.re, mul2(u.im, u.im));
       }
-    }
-    if constexpr (KIND == XP_E || KIND == XP_INV) {
-      if (a.part) {  // float64 mass partial of this tile (renormalisation)
-        double acc = 0.0;
+      if constexpr (KIND == XP_E || KIND == XP_INV) {
+        if (a.part) {  // float64 mass partial of this tile (renormalisation)
+          double acc = 0.0;
 #pragma unroll
-        for (int it = 0; it < 2; ++it)
-#pragma unroll
-          for (int r = 0; r < 4; ++r) acc += (double)rho[it][r].x + (double)rho[it][r].y;
-        acc = block_sum(acc, red);
-        if (tid == 0) a.part[bid] = acc;
+          for (int r = 0; r < 8; ++r) acc += (double)rho[r].x + (double)rho[r].y;
+          acc = block_sum(acc, red);
+          if (tid == 0) a.part[bid] = acc;
+        }
       }
-    }
-    if constexpr (KIND == XP_E) {
-      // the last pass's reads of the tile are finished before it is overwritten
-      __syncthreads();
-      r2c_rows_x2<NX>(a, buf, l0, twb2, rho);
+      if constexpr (KIND == XP_E) {
+        // the densities into the zero-padded packed tile: complex line g
+        // (lines 2g, 2g + 1) is lane g & 1 of slot g >> 1 (the last pass's
+        // reads of the tile are finished before it is overwritten)
+        __syncthreads();
+        float* bf = reinterpret_cast<float*>(buf);
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+          const int sl = pslot<K::NP2>(j + 64 * r, g >> 1) * 4 + (g & 1);
+          bf[sl] = rho[r].x;
+          bf[sl + 2] = rho[r].y;
+        }
+        r2c_rows_staged<NX>(a, buf, l0, twb2);
+      }
+    } else {
+      constexpr bool SLOT = KIND == XP_E;
+      P2 out[2][4];
+      plast_pass<DIR, true, SLOT>(buf, twb1, out, tid);
+      const int j = SLOT ? tid >> 2 : tid & 63;
+      float2 rho[2][4];
+#pragma unroll
+      for (int it = 0; it < 2; ++it) {
+        const int g = 2 * (SLOT ? tid & 3 : tid >> 6) + it;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const P2 u = out[it][r];
+          if (2 * g < nl) line0[(2 * g) * NX + j + 64 * r] = make_float2(u.re.x, u.im.x);
+          if (2 * g + 1 < nl) line0[(2 * g + 1) * NX + j + 64 * r] = make_float2(u.re.y, u.im.y);
+          rho[it][r] = fma2(u.re, u.re, mul2(u.im, u.im));
+        }
+      }
+      if constexpr (KIND == XP_E || KIND == XP_INV) {
+        if (a.part) {  // float64 mass partial of this tile (renormalisation)
+          double acc = 0.0;
+#pragma unroll
+          for (int it = 0; it < 2; ++it)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc += (double)rho[it][r].x + (double)rho[it][r].y;
+          acc = block_sum(acc, red);
+          if (tid == 0) a.part[bid] = acc;
+        }
+      }
+      if constexpr (KIND == XP_E) {
+        // the last pass's reads of the tile are finished before it is overwritten
+        __syncthreads();
+        r2c_rows_x2<NX>(a, buf, l0, twb2, rho);
+      }
     }
   } else {
     static_assert(KIND == XP_A, "packed x passes: X0, XI, E, A");
@@ -419,18 +497,30 @@ __device__ __forceinline__ void xpass_body_x2(const XArgs& a, const float2* __re
     __syncthreads();
     pstockham_pass<NX, NP, NT, -1, true, 8, 1, false, false>(buf, twb1);
     pstockham_pass<NX, NP, NT, -1, true, 8, 8, false, false>(buf, twb1);
-    P2 out[2][4];
-    plast_pass<-1, true>(buf, twb1, out, tid);
     float2* line0 = reinterpret_cast<float2*>(a.psi) + (long long)l0 * NX;
-    const int j = tid & 63;
+    if constexpr (NX == 512) {
+      // last pass (radix 8, stride 64): pair t / 64, positions t % 64 + 64 r
+      const int g = tid >> 6, j = tid & 63;
+      P2 o[8];
+      preg_last<NX, 8, -1, true>(buf, twb1, o, g, j);
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      const int g = 2 * (tid >> 6) + it;
+      for (int r = 0; r < 8; ++r) {
+        if (2 * g < nl) line0[(2 * g) * NX + j + 64 * r] = make_float2(o[r].re.x, o[r].im.x);
+        if (2 * g + 1 < nl) line0[(2 * g + 1) * NX + j + 64 * r] = make_float2(o[r].re.y, o[r].im.y);
+      }
+    } else {
+      P2 out[2][4];
+      plast_pass<-1, true>(buf, twb1, out, tid);
+      const int j = tid & 63;
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const P2 u = out[it][r];
-        if (2 * g < nl) line0[(2 * g) * NX + j + 64 * r] = make_float2(u.re.x, u.im.x);
-        if (2 * g + 1 < nl) line0[(2 * g + 1) * NX + j + 64 * r] = make_float2(u.re.y, u.im.y);
+      for (int it = 0; it < 2; ++it) {
+        const int g = 2 * (tid >> 6) + it;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const P2 u = out[it][r];
+          if (2 * g < nl) line0[(2 * g) * NX + j + 64 * r] = make_float2(u.re.x, u.im.x);
+          if (2 * g + 1 < nl) line0[(2 * g + 1) * NX + j + 64 * r] = make_float2(u.re.y, u.im.y);
+        }
       }
     }
   }
