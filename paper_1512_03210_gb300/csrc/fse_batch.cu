@@ -63,13 +63,22 @@ k_xpass_batch(XArgs a, const typename Cplx<Real>::T* __restrict__ twn, const typ
   if constexpr (KIND == XP_A) {
     // exact time integral of the rotating harmonic trap over the run's step
     // (Eq. int_poten); the call's start time t0 is a device scalar, so that a
-    // captured graph of the step sequence serves every call
-    const double ta = *t0p + step * r.dt, d = r.dt, mid = 2.0 * ta + d;
-    const double C2 = cos(r.omega * mid) * sin_over_dev(r.omega, d);
-    const double S2 = sin(r.omega * mid) * sin_over_dev(r.omega, d);
-    a.pa = 0.25 * (r.gx2 * (d + C2) + r.gy2 * (d - C2));
-    a.pb = 0.25 * (r.gx2 * (d - C2) + r.gy2 * (d + C2));
-    a.pc = 0.5 * (r.gx2 - r.gy2) * S2;
+    // captured graph of the step sequence serves every call. One thread
+    // evaluates the float64 sines and cosines (GB300's float64 pipe is
+    // narrow) and the block reads the coefficients from shared memory.
+    __shared__ double trap[3];
+    if (threadIdx.x == 0) {
+      const double ta = *t0p + step * r.dt, d = r.dt, mid = 2.0 * ta + d;
+      const double C2 = cos(r.omega * mid) * sin_over_dev(r.omega, d);
+      const double S2 = sin(r.omega * mid) * sin_over_dev(r.omega, d);
+      trap[0] = 0.25 * (r.gx2 * (d + C2) + r.gy2 * (d - C2));
+      trap[1] = 0.25 * (r.gx2 * (d - C2) + r.gy2 * (d + C2));
+      trap[2] = 0.5 * (r.gx2 - r.gy2) * S2;
+    }
+    __syncthreads();
+    a.pa = trap[0];
+    a.pb = trap[1];
+    a.pc = trap[2];
     a.pe = 0.0;
     a.beta_dt = r.beta * r.dt;
     a.lam = r.lam;
