@@ -39,7 +39,7 @@ typedef struct fse_plan* fse_plan_t;
 typedef enum {
   FSE_OK = 0,
   FSE_ERR_INVALID = 1,      /* a null pointer, a bad parameter or call order */
-  FSE_ERR_UNSUPPORTED = 2,  /* a valid request this build does not implement */
+  FSE_ERR_UNSUPPORTED = 2,  /* a valid request the library does not implement */
   FSE_ERR_NOMEM = 3,        /* the workspace given is smaller than required */
   FSE_ERR_CUDA = 4,         /* a CUDA runtime call failed (message in fse_plan_error) */
   FSE_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
