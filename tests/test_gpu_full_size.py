@@ -3,7 +3,8 @@
 The 256^3 dipolar step runs the column passes at length 512 along both
 padded axes (F and H along y, G along z: k_colpass<Real, 512, 2/3/5>), the
 kinetic passes at length 256 (B, C, D) and the x passes at n_x = 256 (E and
-A, whose packed real transforms have length 512). Each test below drives one
+A, whose packed real transforms have length 512); the batched workload's
+largest runs take the packed x passes at n_x = 512. Each test below drives one
 of those axes at its benchmark length on a grid the oracle finishes in
 seconds, in float32 and float64, element by element; then the benchmark
 workload itself (256^3, two steps, so that the merged kinetic half step runs)
@@ -54,11 +55,13 @@ def _gpu(lib, d, psi0, t0, nsteps):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
-@pytest.mark.parametrize("n", [(16, 16, 256), (16, 256, 16), (256, 16, 16), (48, 24, 256), (24, 256, 48)],
-                         ids=["z512", "y512", "x256", "z512-ragged", "y512-ragged"])
+@pytest.mark.parametrize("n", [(16, 16, 256), (16, 256, 16), (256, 16, 16), (48, 24, 256), (24, 256, 48),
+                               (512, 8, 8)],
+                         ids=["z512", "y512", "x256", "z512-ragged", "y512-ragged", "x512"])
 def test_benchmark_lengths_match_oracle(lib, n, prec):
     """Length-512 padded transforms along z (pass G) and y (F, H), length-256
-    kinetic transforms (B, C, D) and n_x = 256 x passes (E, A)."""
+    kinetic transforms (B, C, D) and n_x = 256 x passes (E, A); the packed x
+    passes at n_x = 512 (16-line tiles of 512 threads) in 3D."""
     d = _case(n, prec)
     p = O.params(d)
     psi0 = _state(d, sum(n))
@@ -66,6 +69,20 @@ def test_benchmark_lengths_match_oracle(lib, n, prec):
     got = _gpu(lib, d, psi0, 0.1, 2)
     rel, elem = bounds(prec, 2)
     assert_parity(got, ref, rel, elem, f"{n} {prec}")
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_2d_x512_partial_tile_matches_oracle(lib, prec):
+    """2D at n = (512, 24): 24 lines, so the second 16-line tile of the packed
+    n_x = 512 x passes holds 8 lines (the rest of the tile is not read or written)."""
+    d = dict(dim=2, n=(512, 24), lo=(-16.0, -6.0), hi=(16.0, 6.0), s=0.7, m=0.0, omega=0.5, beta=60.0,
+             lam=10.0, dt=1e-3, kernel="coulomb", gamma=(1.0, 1.5), prec=prec)
+    p = O.params(d)
+    psi0 = _state(d, 24)
+    ref = O.evolve(psi0, p, 0.0, 3)
+    got = _gpu(lib, d, psi0, 0.0, 3)
+    rel, elem = bounds(prec, 3)
+    assert_parity(got, ref, rel, elem, f"2d (512, 24) {prec}")
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
